@@ -1,0 +1,171 @@
+"""CPU oracle for the hashed-TSDF per-frame core (allocation, integration,
+raycast) of InfiniTAM v3, Sec. 3-4.
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+bench's CPU-baseline leg are the only callers.  The product path never
+imports this package.  The arithmetic lives in ``itm_oracle.c`` (plain C,
+single-threaded, fp32 with every operation rounded separately, as the paper's
+listings are written in float); this module only marshals numpy arrays.
+
+Every function here is pinned by tests in ``tests/test_oracle_pins.py``
+against closed forms, brute force and analytic geometry; see the docstrings
+there for which pin covers which step.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "itm_oracle.c")
+_LIB_DIR = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_LIB_DIR, "liboracle.so")
+
+CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
+
+ST_HASH_FULL = 1
+ST_VBA_FULL = 2
+ST_RANGE = 4
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (no FMA contraction) into oracle/_build."""
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = ctypes.CDLL(build())
+    P = ctypes.c_void_p
+    f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+    i16p = np.ctypeslib.ndpointer(np.int16, flags="C_CONTIGUOUS")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    u16p = np.ctypeslib.ndpointer(np.uint16, flags="C_CONTIGUOUS")
+    lib.orc_hash_index.restype = ctypes.c_uint32
+    lib.orc_hash_index.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint32]
+    lib.orc_scene_new.restype = P
+    lib.orc_scene_new.argtypes = [ctypes.c_float, ctypes.c_float, ctypes.c_int, ctypes.c_int,
+                                  ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.c_float]
+    lib.orc_scene_free.argtypes = [P]
+    lib.orc_allocate.restype = ctypes.c_int
+    lib.orc_allocate.argtypes = [P, f32p, ctypes.c_int, ctypes.c_int, f32p, f32p]
+    lib.orc_integrate.restype = ctypes.c_longlong
+    lib.orc_integrate.argtypes = [P, f32p, ctypes.c_int, ctypes.c_int, f32p, f32p, P]
+    lib.orc_raycast.restype = ctypes.c_int
+    lib.orc_raycast.argtypes = [P, ctypes.c_int, ctypes.c_int, f32p, f32p, f32p, f32p]
+    lib.orc_status.restype = ctypes.c_int
+    lib.orc_status.argtypes = [P]
+    lib.orc_num_allocated.restype = ctypes.c_int
+    lib.orc_num_allocated.argtypes = [P]
+    lib.orc_excess_used.restype = ctypes.c_int
+    lib.orc_excess_used.argtypes = [P]
+    lib.orc_export.restype = ctypes.c_int
+    lib.orc_export.argtypes = [P, i16p, P, P, ctypes.c_int]
+    lib.orc_entries.argtypes = [P, i32p]
+    lib.orc_depth_u16_to_f32.argtypes = [u16p, f32p, ctypes.c_longlong]
+    _lib = lib
+    return lib
+
+
+def hash_index(x: int, y: int, z: int, num_buckets: int) -> int:
+    return int(_load().orc_hash_index(int(x), int(y), int(z), num_buckets - 1))
+
+
+def depth_u16_to_f32(raw: np.ndarray) -> np.ndarray:
+    raw = np.ascontiguousarray(raw, dtype=np.uint16)
+    out = np.empty(raw.shape, dtype=np.float32)
+    _load().orc_depth_u16_to_f32(raw.ravel(), out.ravel(), raw.size)
+    return out
+
+
+def _f32(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+class Scene:
+    """One hashed TSDF volume held by the oracle."""
+
+    def __init__(self, voxel_size, mu, max_w, num_buckets, num_excess, num_blocks,
+                 z_min, z_max, **_ignored):
+        lib = _load()
+        self.p = lib.orc_scene_new(voxel_size, mu, int(max_w), int(num_buckets), int(num_excess),
+                                   int(num_blocks), z_min, z_max)
+        if not self.p:
+            raise ValueError("invalid scene parameters")
+        self.params = dict(voxel_size=voxel_size, mu=mu, max_w=max_w, num_buckets=num_buckets,
+                           num_excess=num_excess, num_blocks=num_blocks, z_min=z_min, z_max=z_max)
+
+    def __del__(self):
+        if getattr(self, "p", None):
+            _load().orc_scene_free(self.p)
+            self.p = None
+
+    def allocate(self, depth, intr, T_wc) -> int:
+        d = _f32(depth)
+        H, W = d.shape
+        return _load().orc_allocate(self.p, d, W, H, _f32(intr), _f32(T_wc).ravel())
+
+    def integrate(self, depth, intr, T_wc, wpx=None) -> int:
+        d = _f32(depth)
+        H, W = d.shape
+        wp = None
+        if wpx is not None:
+            wpx = _f32(wpx)
+            assert wpx.shape == d.shape
+            wp = wpx.ctypes.data
+        return int(_load().orc_integrate(self.p, d, W, H, _f32(intr), _f32(T_wc).ravel(), wp))
+
+    def raycast(self, W, H, intr, T_wc):
+        vtx = np.zeros((H, W, 4), dtype=np.float32)
+        nrm = np.zeros((H, W, 4), dtype=np.float32)
+        _load().orc_raycast(self.p, W, H, _f32(intr), _f32(T_wc).ravel(), vtx, nrm)
+        return vtx, nrm
+
+    def process(self, depth, intr, T_wc, raycast=True, wpx=None):
+        """One frame of the per-frame core: allocate, integrate, raycast."""
+        st = self.allocate(depth, intr, T_wc)
+        n = self.integrate(depth, intr, T_wc, wpx)
+        out = self.raycast(depth.shape[1], depth.shape[0], intr, T_wc) if raycast else None
+        return st, n, out
+
+    @property
+    def status(self) -> int:
+        return _load().orc_status(self.p)
+
+    @property
+    def num_allocated(self) -> int:
+        return _load().orc_num_allocated(self.p)
+
+    @property
+    def excess_used(self) -> int:
+        return _load().orc_excess_used(self.p)
+
+    def export(self, with_voxels=True):
+        """(coords int16 [n,3], sdf float32 [n,512], w float32 [n,512]) in
+        allocation order."""
+        n = self.num_allocated
+        coords = np.zeros((n, 3), dtype=np.int16)
+        sdf = np.zeros((n, 512), dtype=np.float32) if with_voxels else None
+        w = np.zeros((n, 512), dtype=np.float32) if with_voxels else None
+        _load().orc_export(self.p, coords, sdf.ctypes.data if with_voxels else None,
+                           w.ctypes.data if with_voxels else None, n)
+        return coords, sdf, w
+
+    def entries(self) -> np.ndarray:
+        nb, ne = self.params["num_buckets"], self.params["num_excess"]
+        out = np.zeros((nb + ne, 5), dtype=np.int32)
+        _load().orc_entries(self.p, out)
+        return out

@@ -1,0 +1,601 @@
+/*
+ * itm_oracle.c -- plain, slow, single-threaded CPU oracle for the hashed-TSDF
+ * per-frame core of InfiniTAM v3 (Prisacariu et al., 2017).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the tests, the package's smoke check and the
+ * bench's CPU-baseline leg may load this library.  It shares no code, header,
+ * table or constant with the CUDA path; both sides receive the same seeded
+ * inputs (depth frames, poses, parameters) and nothing else.
+ *
+ * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC
+ * (no FMA contraction: every float operation below is rounded on its own, in
+ * the order written, which is what makes the integer decisions reproducible).
+ *
+ * What each function follows:
+ *   orc_hash_index        Sec. 3.2, the printed hashIndex function
+ *   lookup / insert       Sec. 3.3 (retrieval walks bucket then excess chain,
+ *                         excess entry k >= 1 lives at num_buckets + k - 1,
+ *                         a chain ends when offset < 1; insertion reserves
+ *                         from prepopulated free lists)
+ *   orc_allocate          Sec. 4.2 (segment d-mu .. d+mu per depth pixel,
+ *                         every intersected block allocated)
+ *   orc_integrate         Sec. 4.3 listing computeUpdatedVoxelDepthInfo
+ *   orc_raycast           Sec. 4.4 state machine + two trilinear steps
+ *   orc_depth_u16_to_f32  Sec. 4 (ViewBuilder: unsigned short -> float depth)
+ *
+ * Readings taken where the paper is silent (each one is also listed in the
+ * repository's design notes):
+ *   - voxel g (global integer index) sits at world position (float)g * s
+ *     (corner convention); block b holds voxels 8b .. 8b+7 per axis;
+ *   - allocation: both ends of the segment are points on the pixel's ray at
+ *     z-depth d-mu and d+mu; the blocks between them are enumerated with a
+ *     3D DDA (Amanatides & Woo 1987) that only steps along axes which still
+ *     have blocks left to cover; every block of the union over all pixels is
+ *     allocated (the paper lets intra-frame colliding blocks wait for the next
+ *     frame; here allocation is complete and deterministic);
+ *   - integration visits every allocated block (the paper's visible list is
+ *     an optimisation that must not change the result);
+ *   - depth that is not > 0 (zero, negative or NaN) is no measurement;
+ *   - learned weights: newW = w_px instead of 1, skipped when w_px <= 0;
+ *   - raycast: see the comment above orc_raycast.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_BLOCK 8
+#define ORC_BLOCK3 512
+
+enum {
+    ORC_ST_HASH_FULL = 1,   /* excess list exhausted */
+    ORC_ST_VBA_FULL = 2,    /* voxel block array exhausted */
+    ORC_ST_RANGE = 4,       /* block coordinate outside int16 */
+};
+
+typedef struct {
+    int16_t x, y, z, pad;
+    int32_t offset; /* 0: no successor; k >= 1: next entry at nb + k - 1 */
+    int32_t ptr;    /* >= 0 block index, -1 swapped out, < -1 unallocated */
+} orc_entry;
+
+typedef struct {
+    float voxel_size, mu;
+    int max_w;
+    int nb, ne, nv;
+    float z_min, z_max;
+    orc_entry *entries;
+    int32_t *excess_free; /* stack of free excess slots (0-based), top at excess_top-1 */
+    int excess_top;
+    int32_t *block_free;  /* stack of free block indices, top at block_top-1 */
+    int block_top;
+    float *sdf;           /* nv * 512, initialised when the block is handed out */
+    float *w;
+    int16_t *block_pos;   /* nv * 3: coordinates of the block owning each index */
+    int32_t *alloc_order; /* block indices in order of allocation */
+    int n_alloc;
+    int status;
+} orc_scene;
+
+/* ---------------------------------------------------------------- hashing */
+
+/* Sec. 3.2: xor of the coordinates times three primes, masked by nb-1. */
+uint32_t orc_hash_index(int x, int y, int z, uint32_t mask)
+{
+    uint32_t hx = (uint32_t)x * 73856093u;
+    uint32_t hy = (uint32_t)y * 19349669u;
+    uint32_t hz = (uint32_t)z * 83492791u;
+    return (hx ^ hy ^ hz) & mask;
+}
+
+orc_scene *orc_scene_new(float voxel_size, float mu, int max_w, int nb, int ne, int nv,
+                         float z_min, float z_max)
+{
+    if (nb <= 0 || (nb & (nb - 1)) != 0 || ne < 0 || nv < 0) return NULL;
+    orc_scene *s = (orc_scene *)calloc(1, sizeof(orc_scene));
+    s->voxel_size = voxel_size;
+    s->mu = mu;
+    s->max_w = max_w;
+    s->nb = nb;
+    s->ne = ne;
+    s->nv = nv;
+    s->z_min = z_min;
+    s->z_max = z_max;
+    s->entries = (orc_entry *)malloc(sizeof(orc_entry) * (size_t)(nb + ne));
+    for (int i = 0; i < nb + ne; ++i) {
+        s->entries[i].x = s->entries[i].y = s->entries[i].z = s->entries[i].pad = 0;
+        s->entries[i].offset = 0;
+        s->entries[i].ptr = -2;
+    }
+    s->excess_free = (int32_t *)malloc(sizeof(int32_t) * (size_t)(ne > 0 ? ne : 1));
+    for (int i = 0; i < ne; ++i) s->excess_free[i] = ne - 1 - i; /* pops 0,1,2,... */
+    s->excess_top = ne;
+    s->block_free = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+    for (int i = 0; i < nv; ++i) s->block_free[i] = nv - 1 - i;
+    s->block_top = nv;
+    s->sdf = (float *)malloc(sizeof(float) * (size_t)(nv > 0 ? nv : 1) * ORC_BLOCK3);
+    s->w = (float *)malloc(sizeof(float) * (size_t)(nv > 0 ? nv : 1) * ORC_BLOCK3);
+    s->block_pos = (int16_t *)malloc(sizeof(int16_t) * 3 * (size_t)(nv > 0 ? nv : 1));
+    s->alloc_order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(nv > 0 ? nv : 1));
+    return s;
+}
+
+void orc_scene_free(orc_scene *s)
+{
+    if (!s) return;
+    free(s->entries);
+    free(s->excess_free);
+    free(s->block_free);
+    free(s->sdf);
+    free(s->w);
+    free(s->block_pos);
+    free(s->alloc_order);
+    free(s);
+}
+
+/* Sec. 3.3 retrieval: bucket, then the excess chain.  Returns the block index
+ * (>= 0) or -1 when the block is not present. */
+static int lookup(const orc_scene *s, int bx, int by, int bz)
+{
+    int idx = (int)orc_hash_index(bx, by, bz, (uint32_t)(s->nb - 1));
+    for (;;) {
+        const orc_entry *e = &s->entries[idx];
+        if (e->x == bx && e->y == by && e->z == bz && e->ptr >= 0) return e->ptr;
+        if (e->offset < 1) return -1;
+        idx = s->nb + e->offset - 1;
+    }
+}
+
+static int take_block(orc_scene *s, int bx, int by, int bz)
+{
+    if (s->block_top <= 0) {
+        s->status |= ORC_ST_VBA_FULL;
+        return -1;
+    }
+    int ptr = s->block_free[--s->block_top];
+    for (int i = 0; i < ORC_BLOCK3; ++i) {
+        s->sdf[(size_t)ptr * ORC_BLOCK3 + i] = 1.0f; /* Sec. 3.1: float sdf starts at 1 */
+        s->w[(size_t)ptr * ORC_BLOCK3 + i] = 0.0f;
+    }
+    s->block_pos[3 * ptr + 0] = (int16_t)bx;
+    s->block_pos[3 * ptr + 1] = (int16_t)by;
+    s->block_pos[3 * ptr + 2] = (int16_t)bz;
+    s->alloc_order[s->n_alloc++] = ptr;
+    return ptr;
+}
+
+/* Sec. 3.3 insertion: claim the bucket if it is free, otherwise walk to the
+ * chain's end, reserve an excess entry and link it from the last entry. */
+static void insert_if_missing(orc_scene *s, int bx, int by, int bz)
+{
+    int idx = (int)orc_hash_index(bx, by, bz, (uint32_t)(s->nb - 1));
+    orc_entry *e = &s->entries[idx];
+    if (e->ptr < -1) { /* the bucket itself is unused */
+        if (s->block_top <= 0) {
+            s->status |= ORC_ST_VBA_FULL;
+            return;
+        }
+        e->x = (int16_t)bx;
+        e->y = (int16_t)by;
+        e->z = (int16_t)bz;
+        e->ptr = take_block(s, bx, by, bz);
+        return;
+    }
+    for (;;) {
+        if (e->x == bx && e->y == by && e->z == bz) return; /* present */
+        if (e->offset < 1) break;
+        e = &s->entries[s->nb + e->offset - 1];
+    }
+    if (s->excess_top <= 0) {
+        s->status |= ORC_ST_HASH_FULL;
+        return;
+    }
+    if (s->block_top <= 0) {
+        s->status |= ORC_ST_VBA_FULL;
+        return;
+    }
+    int slot = s->excess_free[--s->excess_top];
+    orc_entry *n = &s->entries[s->nb + slot];
+    n->x = (int16_t)bx;
+    n->y = (int16_t)by;
+    n->z = (int16_t)bz;
+    n->offset = 0;
+    n->ptr = take_block(s, bx, by, bz);
+    e->offset = slot + 1;
+}
+
+/* ------------------------------------------------------------ pose helpers */
+
+/* M = T^-1 for a rigid camera-to-world T, computed in fp64 as [R^T, -R^T t]
+ * and rounded once to float. */
+static void rigid_inverse(const float T[16], float M[16])
+{
+    double R[3][3], t[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) R[i][j] = (double)T[4 * i + j];
+        t[i] = (double)T[4 * i + 3];
+    }
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) M[4 * i + j] = (float)R[j][i];
+        double acc = 0.0;
+        for (int j = 0; j < 3; ++j) acc -= R[j][i] * t[j];
+        M[4 * i + 3] = (float)acc;
+    }
+    M[12] = M[13] = M[14] = 0.0f;
+    M[15] = 1.0f;
+}
+
+/* Row i of a 4x4 float matrix applied to (x, y, z, 1): ((a*x + b*y) + c*z) + d,
+ * each operation rounded separately. */
+static float row_apply(const float *m, float x, float y, float z)
+{
+    float a = m[0] * x;
+    float b = m[1] * y;
+    float c = m[2] * z;
+    float r = a + b;
+    r = r + c;
+    r = r + m[3];
+    return r;
+}
+
+static int in_i16(int v) { return v >= -32768 && v <= 32767; }
+
+/* -------------------------------------------------------------- allocation */
+
+/* Blocks crossed by the segment q0 -> q1 (block units), stepping one axis at a
+ * time towards the end block; ties go to x, then y, then z. */
+static void dda_blocks(orc_scene *s, const float q0[3], const float q1[3])
+{
+    int cur[3], end[3], step[3], left[3];
+    float tmax[3], tdelta[3];
+    for (int i = 0; i < 3; ++i) {
+        float f0 = floorf(q0[i]);
+        float f1 = floorf(q1[i]);
+        if (!(f0 >= -32768.0f && f0 <= 32767.0f && f1 >= -32768.0f && f1 <= 32767.0f)) {
+            s->status |= ORC_ST_RANGE;
+            return;
+        }
+        cur[i] = (int)f0;
+        end[i] = (int)f1;
+        float dir = q1[i] - q0[i];
+        if (end[i] > cur[i]) {
+            step[i] = 1;
+            left[i] = end[i] - cur[i];
+            tdelta[i] = 1.0f / dir;
+            tmax[i] = ((float)(cur[i] + 1) - q0[i]) / dir;
+        } else if (end[i] < cur[i]) {
+            step[i] = -1;
+            left[i] = cur[i] - end[i];
+            tdelta[i] = -1.0f / dir;
+            tmax[i] = ((float)cur[i] - q0[i]) / dir;
+        } else {
+            step[i] = 0;
+            left[i] = 0;
+            tdelta[i] = 0.0f;
+            tmax[i] = 0.0f;
+        }
+    }
+    insert_if_missing(s, cur[0], cur[1], cur[2]);
+    while (left[0] + left[1] + left[2] > 0) {
+        int a = -1;
+        for (int i = 0; i < 3; ++i)
+            if (left[i] > 0 && (a < 0 || tmax[i] < tmax[a])) a = i;
+        cur[a] += step[a];
+        tmax[a] = tmax[a] + tdelta[a];
+        left[a] -= 1;
+        insert_if_missing(s, cur[0], cur[1], cur[2]);
+    }
+}
+
+/* Sec. 4.2, first and second parts: for each valid pixel, the line from
+ * depth d-mu to d+mu on the pixel's ray; every block it crosses is looked up
+ * and inserted when missing.  Pixels are visited in row-major order.
+ * Returns the sticky status bits. */
+int orc_allocate(orc_scene *s, const float *depth, int W, int H, const float intr[4],
+                 const float T_wc[16])
+{
+    const float fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3];
+    const float inv_b = (float)(1.0 / (8.0 * (double)s->voxel_size));
+    const float mu = s->mu;
+    for (int v = 0; v < H; ++v) {
+        for (int u = 0; u < W; ++u) {
+            float d = depth[(size_t)v * W + u];
+            if (!(d > 0.0f)) continue;
+            if (d < s->z_min || d > s->z_max) continue;
+            float rx = ((float)u - cx) / fx;
+            float ry = ((float)v - cy) / fy;
+            float z0 = d - mu;
+            float z1 = d + mu;
+            if (z0 < 1e-3f) z0 = 1e-3f;
+            float q0[3], q1[3];
+            for (int i = 0; i < 3; ++i) {
+                float p0 = row_apply(&T_wc[4 * i], rx * z0, ry * z0, z0);
+                float p1 = row_apply(&T_wc[4 * i], rx * z1, ry * z1, z1);
+                q0[i] = p0 * inv_b;
+                q1[i] = p1 * inv_b;
+            }
+            dda_blocks(s, q0, q1);
+        }
+    }
+    return s->status;
+}
+
+/* ------------------------------------------------------------- integration */
+
+/* Sec. 4.3: computeUpdatedVoxelDepthInfo applied to every voxel of every
+ * allocated block.  wpx (nullable) holds a per-pixel observation weight that
+ * replaces the constant 1 (learned-confidence mode).  Returns the number of
+ * voxels updated. */
+long long orc_integrate(orc_scene *s, const float *depth, int W, int H, const float intr[4],
+                        const float T_wc[16], const float *wpx)
+{
+    float M[16];
+    rigid_inverse(T_wc, M);
+    const float fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3];
+    const float mu = s->mu;
+    const float vs = s->voxel_size;
+    const float max_w = (float)s->max_w;
+    const float umax = (float)(W - 2), vmax = (float)(H - 2);
+    long long updated = 0;
+    for (int k = 0; k < s->n_alloc; ++k) {
+        int ptr = s->alloc_order[k];
+        int bx = s->block_pos[3 * ptr], by = s->block_pos[3 * ptr + 1], bz = s->block_pos[3 * ptr + 2];
+        float *F = &s->sdf[(size_t)ptr * ORC_BLOCK3];
+        float *Wt = &s->w[(size_t)ptr * ORC_BLOCK3];
+        for (int lz = 0; lz < 8; ++lz)
+            for (int ly = 0; ly < 8; ++ly)
+                for (int lx = 0; lx < 8; ++lx) {
+                    int i = lx + 8 * ly + 64 * lz;
+                    float px = (float)(bx * 8 + lx) * vs;
+                    float py = (float)(by * 8 + ly) * vs;
+                    float pz = (float)(bz * 8 + lz) * vs;
+                    float X = row_apply(&M[0], px, py, pz);
+                    float Y = row_apply(&M[4], px, py, pz);
+                    float Z = row_apply(&M[8], px, py, pz);
+                    if (Z <= 0.0f) continue;
+                    float u = (fx * X) / Z + cx;
+                    float v = (fy * Y) / Z + cy;
+                    if (u < 1.0f || u > umax || v < 1.0f || v > vmax) continue;
+                    int pix = (int)(u + 0.5f) + (int)(v + 0.5f) * W;
+                    float d = depth[pix];
+                    if (!(d > 0.0f)) continue;
+                    float eta = d - Z;
+                    if (eta < -mu) continue;
+                    float obs = 1.0f;
+                    if (wpx) {
+                        obs = wpx[pix];
+                        if (!(obs > 0.0f)) continue;
+                    }
+                    float f = eta / mu;
+                    if (f > 1.0f) f = 1.0f;
+                    float oldW = Wt[i];
+                    float num = oldW * F[i] + obs * f;
+                    float den = oldW + obs;
+                    F[i] = num / den;
+                    Wt[i] = den < max_w ? den : max_w;
+                    ++updated;
+                }
+    }
+    return updated;
+}
+
+/* ----------------------------------------------------------------- raycast */
+
+/* The TSDF as a field: the stored value of voxel g when its block is
+ * allocated, otherwise the default voxel's value 1 (Sec. 3.3: retrieval of a
+ * missing block returns a default-constructed voxel). */
+static float voxel_value(const orc_scene *s, int gx, int gy, int gz, int *observed)
+{
+    int ptr = lookup(s, gx >> 3, gy >> 3, gz >> 3);
+    if (ptr < 0) {
+        *observed = 0;
+        return 1.0f;
+    }
+    size_t i = (size_t)ptr * ORC_BLOCK3 + (gx & 7) + 8 * (gy & 7) + 64 * (gz & 7);
+    *observed = s->w[i] > 0.0f;
+    return s->sdf[i];
+}
+
+static int coord_ok(float q) { return q > -262000.0f && q < 262000.0f; }
+
+static float lerpf(float a, float b, float t) { return a + t * (b - a); }
+
+/* Trilinear interpolation of the field at voxel coordinates q.  *all_obs is
+ * cleared when one of the eight voxels is unallocated or was never observed. */
+static float trilinear(const orc_scene *s, const float q[3], int *all_obs)
+{
+    float g0f[3], fr[3];
+    for (int i = 0; i < 3; ++i) {
+        g0f[i] = floorf(q[i]);
+        fr[i] = q[i] - g0f[i];
+    }
+    int x = (int)g0f[0], y = (int)g0f[1], z = (int)g0f[2];
+    int o[8];
+    float c000 = voxel_value(s, x, y, z, &o[0]), c100 = voxel_value(s, x + 1, y, z, &o[1]);
+    float c010 = voxel_value(s, x, y + 1, z, &o[2]), c110 = voxel_value(s, x + 1, y + 1, z, &o[3]);
+    float c001 = voxel_value(s, x, y, z + 1, &o[4]), c101 = voxel_value(s, x + 1, y, z + 1, &o[5]);
+    float c011 = voxel_value(s, x, y + 1, z + 1, &o[6]), c111 = voxel_value(s, x + 1, y + 1, z + 1, &o[7]);
+    for (int i = 0; i < 8; ++i) *all_obs &= o[i];
+    float c00 = lerpf(c000, c100, fr[0]);
+    float c10 = lerpf(c010, c110, fr[0]);
+    float c01 = lerpf(c001, c101, fr[0]);
+    float c11 = lerpf(c011, c111, fr[0]);
+    float c0 = lerpf(c00, c10, fr[1]);
+    float c1 = lerpf(c01, c11, fr[1]);
+    return lerpf(c0, c1, fr[2]);
+}
+
+enum { SEARCH_BLOCK_COARSE = 0, SEARCH_BLOCK_FINE, SEARCH_SURFACE, BEHIND_SURFACE, WRONG_SIDE };
+
+/*
+ * Sec. 4.4 raycast.  Readings (the paper names the states and the step
+ * policy but not the constants):
+ *   ray of pixel (u, v): o + t * dir, dir = R ((u-cx)/fx, (v-cy)/fy, 1), so t
+ *   is z-depth; len = |((u-cx)/fx, (v-cy)/fy, 1)|; metric steps are divided by
+ *   len once per ray: tB = 8s/len, tmu = mu/len, ts = s/len.
+ *   t starts at z_min; the ray misses once t > z_max.
+ *   Voxel coordinates q = p * (1/s); "the block at p" is the block of the
+ *   nearest voxel floor(q + 0.5).
+ *   COARSE : block unallocated -> t += tB; allocated -> t -= tB, go FINE.
+ *   FINE   : block unallocated -> t += tmu; allocated -> read F (trilinear):
+ *            F <= 0 -> WRONG_SIDE (no hit); else go SURFACE at the same t.
+ *   SURFACE: block unallocated -> go COARSE (t unchanged); else read F
+ *            (trilinear): F <= 0 -> BEHIND_SURFACE; else t += max(F*tmu, ts).
+ *   BEHIND : twice t += F(t) * tmu with trilinear F; hit point o + t * dir.
+ *   Normal : central differences of the trilinear field at +-1 voxel along
+ *            each world axis, normalised.  No normal when the gradient is
+ *            zero or when one of the 48 voxels read is unallocated or has
+ *            weight 0 (its value is the default 1, not a measurement).
+ *   At most 4*(z_max-z_min)/s + 64 iterations, then the ray misses.
+ * Output: float4 per pixel, vertex (x, y, z, 1) / (0,0,0,0) on a miss and
+ * normal (nx, ny, nz, 1) / (0,0,0,0) when absent.  Returns the hit count.
+ */
+int orc_raycast(const orc_scene *s, int W, int H, const float intr[4], const float T_wc[16],
+                float *vtx, float *nrm)
+{
+    const float fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3];
+    const float vs = s->voxel_size;
+    const float inv_s = (float)(1.0 / (double)vs);
+    const float B = 8.0f * vs;
+    const float mu = s->mu;
+    const int max_iter = (int)(4.0f * (s->z_max - s->z_min) / vs) + 64;
+    int hits = 0;
+    for (int v = 0; v < H; ++v) {
+        for (int u = 0; u < W; ++u) {
+            size_t o4 = 4 * ((size_t)v * W + u);
+            vtx[o4] = vtx[o4 + 1] = vtx[o4 + 2] = vtx[o4 + 3] = 0.0f;
+            nrm[o4] = nrm[o4 + 1] = nrm[o4 + 2] = nrm[o4 + 3] = 0.0f;
+            float dc0 = ((float)u - cx) / fx;
+            float dc1 = ((float)v - cy) / fy;
+            float len = sqrtf((dc0 * dc0 + dc1 * dc1) + 1.0f);
+            float dir[3], org[3];
+            for (int i = 0; i < 3; ++i) {
+                dir[i] = (T_wc[4 * i] * dc0 + T_wc[4 * i + 1] * dc1) + T_wc[4 * i + 2];
+                org[i] = T_wc[4 * i + 3];
+            }
+            const float tB = B / len, tmu = mu / len, ts = vs / len;
+            float t = s->z_min;
+            int state = SEARCH_BLOCK_COARSE;
+            float q[3];
+            int it = 0;
+            for (; it < max_iter && t <= s->z_max; ++it) {
+                int ok = 1;
+                for (int i = 0; i < 3; ++i) {
+                    q[i] = (org[i] + t * dir[i]) * inv_s;
+                    ok &= coord_ok(q[i]);
+                }
+                int alloc = 0;
+                if (ok) {
+                    int nx = (int)floorf(q[0] + 0.5f), ny = (int)floorf(q[1] + 0.5f), nz = (int)floorf(q[2] + 0.5f);
+                    int bx = nx >> 3, by = ny >> 3, bz = nz >> 3;
+                    alloc = in_i16(bx) && in_i16(by) && in_i16(bz) && lookup(s, bx, by, bz) >= 0;
+                }
+                if (state == SEARCH_BLOCK_COARSE) {
+                    if (!alloc) {
+                        t = t + tB;
+                    } else {
+                        t = t - tB;
+                        state = SEARCH_BLOCK_FINE;
+                    }
+                    continue;
+                }
+                if (!alloc) {
+                    if (state == SEARCH_BLOCK_FINE) t = t + tmu;
+                    else state = SEARCH_BLOCK_COARSE;
+                    continue;
+                }
+                int obs = 1;
+                float F = trilinear(s, q, &obs);
+                if (state == SEARCH_BLOCK_FINE) {
+                    if (F <= 0.0f) {
+                        state = WRONG_SIDE;
+                        break;
+                    }
+                    state = SEARCH_SURFACE;
+                }
+                if (F <= 0.0f) {
+                    state = BEHIND_SURFACE;
+                    break;
+                }
+                float step = F * tmu;
+                if (step < ts) step = ts;
+                t = t + step;
+            }
+            if (state != BEHIND_SURFACE) continue;
+            for (int r = 0; r < 2; ++r) {
+                for (int i = 0; i < 3; ++i) q[i] = (org[i] + t * dir[i]) * inv_s;
+                int obs = 1;
+                float F = trilinear(s, q, &obs);
+                t = t + F * tmu;
+            }
+            float p[3];
+            for (int i = 0; i < 3; ++i) {
+                p[i] = org[i] + t * dir[i];
+                q[i] = p[i] * inv_s;
+            }
+            if (!(coord_ok(q[0]) && coord_ok(q[1]) && coord_ok(q[2]))) continue;
+            vtx[o4] = p[0];
+            vtx[o4 + 1] = p[1];
+            vtx[o4 + 2] = p[2];
+            vtx[o4 + 3] = 1.0f;
+            ++hits;
+            float g[3];
+            int obs = 1;
+            for (int a = 0; a < 3; ++a) {
+                float qp[3] = {q[0], q[1], q[2]}, qm[3] = {q[0], q[1], q[2]};
+                qp[a] = q[a] + 1.0f;
+                qm[a] = q[a] - 1.0f;
+                float fp = trilinear(s, qp, &obs);
+                float fm = trilinear(s, qm, &obs);
+                g[a] = fp - fm;
+            }
+            float gl = sqrtf((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);
+            if (obs && gl > 0.0f) {
+                nrm[o4] = g[0] / gl;
+                nrm[o4 + 1] = g[1] / gl;
+                nrm[o4 + 2] = g[2] / gl;
+                nrm[o4 + 3] = 1.0f;
+            }
+        }
+    }
+    return hits;
+}
+
+/* ---------------------------------------------------------- introspection */
+
+int orc_status(const orc_scene *s) { return s->status; }
+int orc_num_allocated(const orc_scene *s) { return s->n_alloc; }
+int orc_excess_used(const orc_scene *s) { return s->ne - s->excess_top; }
+
+/* Copies out the allocated blocks in allocation order: coords (3 x int16),
+ * sdf and weight (512 floats each, voxel index x + 8y + 64z). */
+int orc_export(const orc_scene *s, int16_t *coords, float *sdf, float *w, int cap)
+{
+    int n = s->n_alloc < cap ? s->n_alloc : cap;
+    for (int k = 0; k < n; ++k) {
+        int ptr = s->alloc_order[k];
+        memcpy(&coords[3 * k], &s->block_pos[3 * ptr], 3 * sizeof(int16_t));
+        if (sdf) memcpy(&sdf[(size_t)k * ORC_BLOCK3], &s->sdf[(size_t)ptr * ORC_BLOCK3], ORC_BLOCK3 * sizeof(float));
+        if (w) memcpy(&w[(size_t)k * ORC_BLOCK3], &s->w[(size_t)ptr * ORC_BLOCK3], ORC_BLOCK3 * sizeof(float));
+    }
+    return n;
+}
+
+/* Raw table: per entry x, y, z, offset, ptr as int32. */
+void orc_entries(const orc_scene *s, int32_t *out)
+{
+    for (int i = 0; i < s->nb + s->ne; ++i) {
+        out[5 * i + 0] = s->entries[i].x;
+        out[5 * i + 1] = s->entries[i].y;
+        out[5 * i + 2] = s->entries[i].z;
+        out[5 * i + 3] = s->entries[i].offset;
+        out[5 * i + 4] = s->entries[i].ptr;
+    }
+}
+
+/* The depth value of a raw sensor reading in millimetres: raw / 1000,
+ * correctly rounded (Sec. 4, view preparation). */
+void orc_depth_u16_to_f32(const uint16_t *raw, float *out, long long n)
+{
+    for (long long i = 0; i < n; ++i) out[i] = (float)raw[i] / 1000.0f;
+}
