@@ -1,0 +1,205 @@
+/*
+ * itm.h -- C ABI of the GB300 hashed-TSDF library (libitm.so).
+ *
+ * The library implements the per-frame data-parallel core of voxel-hashing
+ * reconstruction described in InfiniTAM v3 (Prisacariu et al., 2017):
+ * allocation of voxel blocks into a spatial hash (Sec. 4.2, hash structure of
+ * Sec. 3.2-3.3), TSDF/weight integration over the visible blocks (Sec. 4.3)
+ * and raycasting the volume into vertex and normal maps (Sec. 4.4).
+ *
+ * Conventions shared by every call:
+ *  - Camera frame: +x right, +y down, +z forward; u = fx*X/Z + cx,
+ *    v = fy*Y/Z + cy; pixel (u, v) is column u, row v.
+ *  - A pose T_wc is a rigid camera-to-world 4x4 matrix, float[16], row-major,
+ *    passed as a HOST pointer and read before the call returns.  The library
+ *    forms M_d = T_wc^-1 on the host in double precision as [R^T, -R^T t] and
+ *    rounds it to float.
+ *  - Depth images are float32 metres, row-major [height][width], 0 (or any
+ *    value that is not > 0) = no measurement, held in DEVICE memory owned by
+ *    the caller.
+ *  - Output images are DEVICE memory owned by the caller.
+ *  - Every compute call is asynchronous on the given stream (a cudaStream_t
+ *    passed as itm_stream; NULL is the legacy default stream).  Kernel-side
+ *    errors (hash or block array exhausted, coordinate out of range, a bounded
+ *    wait that gave up) set bits in a sticky device status word that is read
+ *    by itm_scene_stats / itm_scene_status, which synchronise the stream.
+ *  - A scene owns all of its device memory; no call after itm_scene_create
+ *    allocates device memory.  Calls on one scene must not overlap in time
+ *    (not thread-safe per scene); different scenes are independent.
+ *  - Return value: ITM_OK or one of the ITM_ERR_* codes below.  A call that
+ *    returns an error has launched nothing.
+ */
+#ifndef ITM_H
+#define ITM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef void *itm_stream; /* a cudaStream_t */
+
+enum {
+    ITM_OK = 0,
+    ITM_ERR_ARG = 1,       /* invalid argument (null pointer, bad size, bad parameter) */
+    ITM_ERR_CUDA = 2,      /* a CUDA runtime call failed */
+    ITM_ERR_HASH_FULL = 3, /* status: excess list exhausted */
+    ITM_ERR_VBA_FULL = 4,  /* status: voxel block array exhausted */
+    ITM_ERR_RANGE = 5,     /* status: block coordinate outside int16 */
+    ITM_ERR_TIMEOUT = 6,   /* status: a bounded device-side wait gave up */
+    ITM_ERR_OVERFLOW = 7,  /* status: a per-frame work list overflowed */
+};
+
+/* Sticky status bits (itm_stats.status). */
+#define ITM_ST_HASH_FULL 0x1u
+#define ITM_ST_VBA_FULL 0x2u
+#define ITM_ST_RANGE 0x4u
+#define ITM_ST_TIMEOUT 0x8u
+#define ITM_ST_OVERFLOW 0x10u
+
+/* Pinhole depth intrinsics (Sec. 6 calibration file: image size, focal
+ * length and principal point in pixels; Sec. 4.3 projParams_d). */
+typedef struct {
+    int width, height;
+    float fx, fy, cx, cy;
+} itm_intrinsics;
+
+/* Scene parameters (Sec. 6 ITMSceneParams; Sec. 3.1 voxel block array size;
+ * Sec. 3.2 bucket count; Sec. 4.3 mu and maxW).
+ *  voxel_size  metres per voxel (s); a block is 8 voxels per axis
+ *  mu          truncation band (metres)
+ *  max_w       weight cap; 1..255 in weight_mode 0
+ *  num_buckets ordered part of the hash table, a power of two
+ *  num_excess  unordered excess entries
+ *  num_blocks  voxel blocks in the block array
+ *  z_min/z_max depth range for allocation and for the raycast march
+ *  weight_mode 0: constant observation weight 1, uint8 weights (Sec. 4.3);
+ *              1: per-pixel observation weight from itm_integrate_weighted,
+ *                 float32 weights */
+typedef struct {
+    float voxel_size, mu;
+    int max_w;
+    int num_buckets, num_excess, num_blocks;
+    float z_min, z_max;
+    int weight_mode;
+} itm_scene_params;
+
+/* Counters kept on the device, cumulative since the last reset unless noted. */
+typedef struct {
+    uint32_t status;            /* sticky ITM_ST_* bits */
+    int32_t allocated_blocks;   /* blocks handed out from the block array */
+    int32_t excess_used;        /* excess entries handed out */
+    int32_t visible_blocks;     /* blocks in the last frame's visible list */
+    int32_t last_requests;      /* new blocks requested by the last allocation */
+    int32_t last_overflow;      /* requests that lost a bucket in the last allocation */
+    uint64_t updated_voxels;    /* voxel updates performed by integration */
+    uint64_t visited_voxels;    /* voxels visited by integration (512 per visible block) */
+    uint64_t frames;            /* completed itm_integrate calls */
+} itm_stats;
+
+typedef struct itm_scene itm_scene;
+
+/* Create a scene on the current CUDA device: allocates the hash table
+ * ((num_buckets + num_excess) entries of 16 bytes: int16 x, y, z, a flag,
+ * int32 offset, int32 ptr; Sec. 3.2), the voxel block array (Sec. 3.1: per
+ * block 512 float sdf + 512 weights), the free lists (Sec. 3.3) and the
+ * per-frame work lists, then resets it and synchronises.  *out receives the
+ * handle.  Errors: ITM_ERR_ARG for invalid parameters, ITM_ERR_CUDA if
+ * device memory cannot be allocated (nothing is leaked). */
+int itm_scene_create(const itm_scene_params *params, itm_scene **out);
+
+/* Release all device memory of the scene (synchronises the device). */
+int itm_scene_destroy(itm_scene *scene);
+
+/* Empty the scene: every entry unallocated (ptr = -2, offset 0), every voxel
+ * sdf = 1, weight = 0 (Sec. 3.1 defaults), full free lists, counters and
+ * status cleared.  Asynchronous on `stream`. */
+int itm_scene_reset(itm_scene *scene, itm_stream stream);
+
+/* Sec. 4.2 allocation.  For each pixel with z_min <= d <= z_max, the blocks
+ * crossed by the segment of the pixel's ray between z-depth d - mu and
+ * d + mu are looked up (Sec. 3.3 retrieval) and every missing one is
+ * inserted (Sec. 3.3 insertion), including blocks that collide in one hash
+ * bucket within the frame.  Then the visible list is rebuilt: every
+ * allocated block whose voxels may project into the image with z > 0 and lie
+ * no further than the frame's largest depth + mu.
+ * depth_dev: device float[height*width].  intr, T_wc: host pointers. */
+int itm_allocate(itm_scene *scene, const float *depth_dev, const itm_intrinsics *intr,
+                 const float T_wc[16], itm_stream stream);
+
+/* Sec. 4.3 integration over the visible list built by the last
+ * itm_allocate: for every voxel, project with M_d = T_wc^-1, skip unless
+ * z > 0, 1 <= u <= W-2, 1 <= v <= H-2, the nearest pixel's depth d > 0 and
+ * eta = d - z >= -mu; then F <- (W F + min(1, eta/mu)) / (W + 1),
+ * W <- min(W + 1, max_w).  Must use the same depth and pose as the
+ * preceding itm_allocate. */
+int itm_integrate(itm_scene *scene, const float *depth_dev, const itm_intrinsics *intr,
+                  const float T_wc[16], itm_stream stream);
+
+/* As itm_integrate, with a per-pixel observation weight w_px (device
+ * float[height*width]) in place of the constant 1: F <- (W F + w_px f) /
+ * (W + w_px), W <- min(W + w_px, max_w); pixels with w_px <= 0 are skipped.
+ * Requires weight_mode 1. */
+int itm_integrate_weighted(itm_scene *scene, const float *depth_dev, const float *wpx_dev,
+                           const itm_intrinsics *intr, const float T_wc[16], itm_stream stream);
+
+/* Sec. 4.4 raycast.  One ray per pixel from the camera centre, marched from
+ * z-depth z_min to z_max through the states SEARCH_BLOCK_COARSE (block-sized
+ * steps through unallocated space), SEARCH_BLOCK_FINE (steps of mu after
+ * stepping back one block), SEARCH_SURFACE (steps of max(F mu, s)) and
+ * BEHIND_SURFACE (first F <= 0), or WRONG_SIDE (negative F on entering a
+ * block: no hit); the hit is refined by two trilinear steps t += F mu.
+ * vertex_dev: device float4[height*width], world (x, y, z, 1) or 0 on a miss.
+ * normal_dev: device float4[height*width], the normalised TSDF gradient by
+ * central differences (x, y, z, 1), or 0 when absent. */
+int itm_raycast(itm_scene *scene, const itm_intrinsics *intr, const float T_wc[16],
+                float *vertex_dev, float *normal_dev, itm_stream stream);
+
+/* One frame of the per-frame core: itm_allocate, itm_integrate and (when
+ * vertex_dev is not NULL) itm_raycast, on one stream. */
+int itm_process_frame(itm_scene *scene, const float *depth_dev, const itm_intrinsics *intr,
+                      const float T_wc[16], float *vertex_dev, float *normal_dev,
+                      itm_stream stream);
+
+/* Sec. 4 view preparation: depth_dev[i] = raw_dev[i] / 1000 (millimetres
+ * to metres, correctly rounded; 0 stays 0).  n elements, device memory. */
+int itm_depth_u16_to_f32(const uint16_t *raw_dev, float *depth_dev, int64_t n, itm_stream stream);
+
+/* Synchronise the scene's last stream and copy the device counters to
+ * *out (host).  Returns ITM_OK, or ITM_ERR_CUDA. */
+int itm_scene_stats(itm_scene *scene, itm_stats *out);
+
+/* Synchronise and translate the sticky status into a return code:
+ * ITM_OK when clear, else the code of the lowest set bit. */
+int itm_scene_status(itm_scene *scene);
+
+/* Copy the allocated blocks to HOST buffers (synchronises): coords_host
+ * int16[cap][3] block coordinates, sdf_host float[cap][512] and w_host
+ * float[cap][512] (either may be NULL), voxel index x + 8y + 64z, in block
+ * array order.  *n receives the number of allocated blocks (which may
+ * exceed cap; only min(n, cap) are written). */
+int itm_scene_export(itm_scene *scene, int16_t *coords_host, float *sdf_host, float *w_host,
+                     int cap, int *n);
+
+/* Copy the raw hash table to a HOST buffer int32[num_buckets + num_excess][5]
+ * (x, y, z, offset, ptr per entry; Sec. 3.2 field meaning).  Synchronises. */
+int itm_scene_export_table(itm_scene *scene, int32_t *entries_host);
+
+/* Reset the scene and insert n blocks from HOST buffers (coords int16[n][3],
+ * sdf float[n][512], w float[n][512]); the inverse of itm_scene_export.
+ * Duplicate coordinates or n > num_blocks give ITM_ERR_ARG.  Synchronises. */
+int itm_scene_import(itm_scene *scene, const int16_t *coords_host, const float *sdf_host,
+                     const float *w_host, int n);
+
+/* The bucket of block (x, y, z) for a table of num_buckets buckets
+ * (Sec. 3.2 hashIndex).  Host function, for tools and tests. */
+uint32_t itm_hash_index(int x, int y, int z, int num_buckets);
+
+/* Library version string. */
+const char *itm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ITM_H */

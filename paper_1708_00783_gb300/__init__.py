@@ -1,0 +1,298 @@
+"""GB300-native hashed-TSDF reconstruction core (InfiniTAM v3, Sec. 3-4).
+
+Python binding of ``libitm.so``: the functions below carry the names of the
+C ABI declared in ``include/itm.h`` and only marshal arguments (device
+pointers of torch tensors, host structs, the current CUDA stream).  Every
+step of the per-frame path runs in the library's CUDA kernels; there is no
+CPU fallback: importing this package fails when the library is missing.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build_mod
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = _build_mod.LIB
+
+ITM_OK = 0
+ERRORS = {1: "ITM_ERR_ARG", 2: "ITM_ERR_CUDA", 3: "ITM_ERR_HASH_FULL", 4: "ITM_ERR_VBA_FULL",
+          5: "ITM_ERR_RANGE", 6: "ITM_ERR_TIMEOUT", 7: "ITM_ERR_OVERFLOW"}
+ST_HASH_FULL, ST_VBA_FULL, ST_RANGE, ST_TIMEOUT, ST_OVERFLOW = 0x1, 0x2, 0x4, 0x8, 0x10
+
+
+class ItmError(RuntimeError):
+    def __init__(self, code, what=""):
+        super().__init__("%s failed: %s (%d)" % (what, ERRORS.get(code, "?"), code))
+        self.code = code
+
+
+class itm_intrinsics(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int), ("height", ctypes.c_int), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float)]
+
+
+class itm_scene_params(ctypes.Structure):
+    _fields_ = [("voxel_size", ctypes.c_float), ("mu", ctypes.c_float), ("max_w", ctypes.c_int),
+                ("num_buckets", ctypes.c_int), ("num_excess", ctypes.c_int), ("num_blocks", ctypes.c_int),
+                ("z_min", ctypes.c_float), ("z_max", ctypes.c_float), ("weight_mode", ctypes.c_int)]
+
+
+class itm_stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_uint32), ("allocated_blocks", ctypes.c_int32),
+                ("excess_used", ctypes.c_int32), ("visible_blocks", ctypes.c_int32),
+                ("last_requests", ctypes.c_int32), ("last_overflow", ctypes.c_int32),
+                ("updated_voxels", ctypes.c_uint64), ("visited_voxels", ctypes.c_uint64),
+                ("frames", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+EXPORTED = [
+    "itm_scene_create", "itm_scene_destroy", "itm_scene_reset", "itm_allocate", "itm_integrate",
+    "itm_integrate_weighted", "itm_raycast", "itm_process_frame", "itm_depth_u16_to_f32",
+    "itm_scene_stats", "itm_scene_status", "itm_scene_export", "itm_scene_export_table",
+    "itm_scene_import", "itm_hash_index", "itm_version",
+]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError("libitm.so is not built (%s); run paper_1708_00783_gb300.build.build()" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    fp16 = ctypes.POINTER(ctypes.c_float)
+    sp = ctypes.POINTER(itm_scene_params)
+    ip = ctypes.POINTER(itm_intrinsics)
+    sig = {
+        "itm_scene_create": (I, [sp, ctypes.POINTER(P)]),
+        "itm_scene_destroy": (I, [P]),
+        "itm_scene_reset": (I, [P, P]),
+        "itm_allocate": (I, [P, P, ip, fp16, P]),
+        "itm_integrate": (I, [P, P, ip, fp16, P]),
+        "itm_integrate_weighted": (I, [P, P, P, ip, fp16, P]),
+        "itm_raycast": (I, [P, ip, fp16, P, P, P]),
+        "itm_process_frame": (I, [P, P, ip, fp16, P, P, P]),
+        "itm_depth_u16_to_f32": (I, [P, P, ctypes.c_int64, P]),
+        "itm_scene_stats": (I, [P, ctypes.POINTER(itm_stats)]),
+        "itm_scene_status": (I, [P]),
+        "itm_scene_export": (I, [P, P, P, P, I, ctypes.POINTER(I)]),
+        "itm_scene_export_table": (I, [P, P]),
+        "itm_scene_import": (I, [P, P, P, P, I]),
+        "itm_hash_index": (ctypes.c_uint32, [I, I, I, I]),
+        "itm_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype, fn.argtypes = res, args
+    return lib
+
+
+_lib = _load()
+
+
+def lib():
+    return _lib
+
+
+# ------------------------------------------------------------ marshalling
+
+def _ptr(x):
+    """Device (or host) address of a torch tensor, numpy array or integer."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError("cannot take the address of %r" % type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _pose(T):
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float32).reshape(16))
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def make_intrinsics(width, height, fx, fy, cx, cy) -> itm_intrinsics:
+    return itm_intrinsics(int(width), int(height), float(fx), float(fy), float(cx), float(cy))
+
+
+def make_params(voxel_size, mu, max_w, num_buckets, num_excess, num_blocks, z_min, z_max,
+                weight_mode=0, **_ignored) -> itm_scene_params:
+    return itm_scene_params(float(voxel_size), float(mu), int(max_w), int(num_buckets), int(num_excess),
+                            int(num_blocks), float(z_min), float(z_max), int(weight_mode))
+
+
+def _check(code, what):
+    if code != ITM_OK:
+        raise ItmError(code, what)
+
+
+# ------------------------------------------------------------ the C ABI
+
+def itm_scene_create(params: itm_scene_params) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.itm_scene_create(ctypes.byref(params), ctypes.byref(h)), "itm_scene_create")
+    return h.value
+
+
+def itm_scene_destroy(scene):
+    _check(_lib.itm_scene_destroy(scene), "itm_scene_destroy")
+
+
+def itm_scene_reset(scene, stream=None):
+    _check(_lib.itm_scene_reset(scene, _stream(stream)), "itm_scene_reset")
+
+
+def itm_allocate(scene, depth, intr, T_wc, stream=None):
+    a, p = _pose(T_wc)
+    _check(_lib.itm_allocate(scene, _ptr(depth), ctypes.byref(intr), p, _stream(stream)), "itm_allocate")
+
+
+def itm_integrate(scene, depth, intr, T_wc, stream=None):
+    a, p = _pose(T_wc)
+    _check(_lib.itm_integrate(scene, _ptr(depth), ctypes.byref(intr), p, _stream(stream)), "itm_integrate")
+
+
+def itm_integrate_weighted(scene, depth, wpx, intr, T_wc, stream=None):
+    a, p = _pose(T_wc)
+    _check(_lib.itm_integrate_weighted(scene, _ptr(depth), _ptr(wpx), ctypes.byref(intr), p, _stream(stream)),
+           "itm_integrate_weighted")
+
+
+def itm_raycast(scene, intr, T_wc, vertex, normal, stream=None):
+    a, p = _pose(T_wc)
+    _check(_lib.itm_raycast(scene, ctypes.byref(intr), p, _ptr(vertex), _ptr(normal), _stream(stream)),
+           "itm_raycast")
+
+
+def itm_process_frame(scene, depth, intr, T_wc, vertex=None, normal=None, stream=None):
+    a, p = _pose(T_wc)
+    _check(_lib.itm_process_frame(scene, _ptr(depth), ctypes.byref(intr), p, _ptr(vertex), _ptr(normal),
+                                  _stream(stream)), "itm_process_frame")
+
+
+def itm_depth_u16_to_f32(raw, out, n=None, stream=None):
+    n = raw.numel() if n is None else n
+    _check(_lib.itm_depth_u16_to_f32(_ptr(raw), _ptr(out), int(n), _stream(stream)), "itm_depth_u16_to_f32")
+
+
+def itm_scene_stats(scene) -> dict:
+    st = itm_stats()
+    _check(_lib.itm_scene_stats(scene, ctypes.byref(st)), "itm_scene_stats")
+    return st.as_dict()
+
+
+def itm_scene_status(scene) -> int:
+    return _lib.itm_scene_status(scene)
+
+
+def itm_scene_export(scene, with_voxels=True):
+    """(coords int16 [n,3], sdf float32 [n,512], w float32 [n,512]) in block
+    array order (host numpy arrays)."""
+    n = ctypes.c_int(0)
+    _check(_lib.itm_scene_export(scene, None, None, None, 0, ctypes.byref(n)), "itm_scene_export")
+    cnt = n.value
+    coords = np.zeros((max(cnt, 1), 3), dtype=np.int16)
+    sdf = np.zeros((max(cnt, 1), 512), dtype=np.float32) if with_voxels else None
+    w = np.zeros((max(cnt, 1), 512), dtype=np.float32) if with_voxels else None
+    _check(_lib.itm_scene_export(scene, coords.ctypes.data, sdf.ctypes.data if with_voxels else None,
+                                 w.ctypes.data if with_voxels else None, cnt, ctypes.byref(n)), "itm_scene_export")
+    if with_voxels:
+        return coords[:cnt], sdf[:cnt], w[:cnt]
+    return coords[:cnt], None, None
+
+
+def itm_scene_export_table(scene, num_buckets, num_excess) -> np.ndarray:
+    out = np.zeros((num_buckets + num_excess, 5), dtype=np.int32)
+    _check(_lib.itm_scene_export_table(scene, out.ctypes.data), "itm_scene_export_table")
+    return out
+
+
+def itm_scene_import(scene, coords, sdf, w):
+    coords = np.ascontiguousarray(coords, dtype=np.int16)
+    sdf = np.ascontiguousarray(sdf, dtype=np.float32)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    n = coords.shape[0]
+    _check(_lib.itm_scene_import(scene, coords.ctypes.data, sdf.ctypes.data, w.ctypes.data, n), "itm_scene_import")
+
+
+def itm_hash_index(x, y, z, num_buckets) -> int:
+    return int(_lib.itm_hash_index(int(x), int(y), int(z), int(num_buckets)))
+
+
+def itm_version() -> str:
+    return _lib.itm_version().decode()
+
+
+# ------------------------------------------------------------ convenience
+
+class Scene:
+    """Owning wrapper of an itm_scene handle."""
+
+    def __init__(self, voxel_size, mu, max_w, num_buckets, num_excess, num_blocks, z_min, z_max,
+                 weight_mode=0, **_ignored):
+        self.params = dict(voxel_size=voxel_size, mu=mu, max_w=max_w, num_buckets=num_buckets,
+                           num_excess=num_excess, num_blocks=num_blocks, z_min=z_min, z_max=z_max,
+                           weight_mode=weight_mode)
+        self.handle = itm_scene_create(make_params(**self.params))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            itm_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def reset(self, stream=None):
+        itm_scene_reset(self.handle, stream)
+
+    def allocate(self, depth, intr, T_wc, stream=None):
+        itm_allocate(self.handle, depth, intr, T_wc, stream)
+
+    def integrate(self, depth, intr, T_wc, stream=None, wpx=None):
+        if wpx is None:
+            itm_integrate(self.handle, depth, intr, T_wc, stream)
+        else:
+            itm_integrate_weighted(self.handle, depth, wpx, intr, T_wc, stream)
+
+    def raycast(self, intr, T_wc, vertex, normal, stream=None):
+        itm_raycast(self.handle, intr, T_wc, vertex, normal, stream)
+
+    def process(self, depth, intr, T_wc, vertex=None, normal=None, stream=None):
+        itm_process_frame(self.handle, depth, intr, T_wc, vertex, normal, stream)
+
+    def stats(self) -> dict:
+        return itm_scene_stats(self.handle)
+
+    def status(self) -> int:
+        return itm_scene_status(self.handle)
+
+    def export(self, with_voxels=True):
+        return itm_scene_export(self.handle, with_voxels)
+
+    def export_table(self):
+        return itm_scene_export_table(self.handle, self.params["num_buckets"], self.params["num_excess"])
+
+    def import_blocks(self, coords, sdf, w):
+        itm_scene_import(self.handle, coords, sdf, w)

@@ -1,0 +1,203 @@
+// Internal definitions shared by the CUDA translation units of libitm.
+//
+// Device layout of one scene (all arrays allocated once by itm_scene_create):
+//   entries     Entry[nb + ne]      16 B each; buckets then excess entries (Sec. 3.2)
+//   req         uint64[nb]          per-bucket allocation request (packed key, 0 = none)
+//   req_list    int32[nb]           buckets that received a request this frame
+//   overflow    uint64[ovf_cap]     requests that lost their bucket to another key
+//   visible     int32[nv]           visible block indices of the current frame
+//   block_pos   short4[nv]          coordinates of the block held at each index (w = 1 in use)
+//   sdf         float[nv][512]      TSDF, voxel index x + 8y + 64z (Sec. 3.1)
+//   w8 / w32    uint8 / float [nv][512]  weights (constant / learned observation weight)
+//   block_free  int32[nv]           free block list, handed out front to back
+//   excess_free int32[ne]           free excess slots, handed out front to back
+//   ctr         Counters            device counters and the sticky status word
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "itm.h"
+
+namespace itm {
+
+constexpr int kBlockVoxels = 512;
+constexpr unsigned kFull = 0xffffffffu;
+
+// Sec. 3.2 hash entry.  Bytes 0..7 (x, y, z, flag) form the packed block key
+// compared and claimed as one 64-bit word; flag = 1 marks an entry that holds
+// a block, so the all-zero word means "never used".
+struct __align__(16) Entry {
+    int16_t x, y, z, flag;
+    int32_t offset;  // 0: end of chain; k >= 1: next entry at nb + k - 1 (Sec. 3.3)
+    int32_t ptr;     // >= 0 block index; -1 swapped out; < -1 unallocated (Sec. 3.2)
+};
+
+struct Counters {
+    uint32_t status;
+    int32_t block_head;     // blocks handed out (may run past nv when the array is full)
+    int32_t excess_head;    // excess slots handed out
+    int32_t n_req;          // per-frame: buckets requested
+    int32_t n_overflow;     // per-frame: requests that lost their bucket
+    int32_t n_visible;      // per-frame: visible blocks
+    int32_t depth_max_bits; // per-frame: largest valid depth (float bits, >= 0)
+    int32_t pad0;
+    unsigned long long updated;  // cumulative voxel updates
+    unsigned long long visited;  // cumulative voxels visited by integration
+    unsigned long long frames;   // cumulative integrated frames
+};
+
+// Offset and size of the per-frame counters cleared at the start of allocation.
+constexpr size_t kFrameCountersOffset = 12;  // n_req
+constexpr size_t kFrameCountersBytes = 16;   // n_req .. depth_max_bits
+
+struct SceneDev {
+    Entry *entries;
+    unsigned long long *req;
+    int32_t *req_list;
+    unsigned long long *overflow;
+    int32_t *visible;
+    short4 *block_pos;
+    float *sdf;
+    uint8_t *w8;
+    float *w32;
+    int32_t *block_free;
+    int32_t *excess_free;
+    Counters *ctr;
+    int nb, ne, nv;
+    int ovf_cap;
+    float voxel_size, mu, z_min, z_max;
+    int max_w, weight_mode;
+};
+
+struct Intr {
+    int W, H;
+    float fx, fy, cx, cy;
+};
+
+// Rows 0..2 of a 4x4 rigid transform, row-major.
+struct Mat34 {
+    float m[12];
+};
+
+// ---------------------------------------------------------------- hashing
+
+// Sec. 3.2 hashIndex: unsigned coordinates times three primes, xor, mask.
+__host__ __device__ __forceinline__ uint32_t hash_bucket(int x, int y, int z, uint32_t mask)
+{
+    return (((uint32_t)x * 73856093u) ^ ((uint32_t)y * 19349669u) ^ ((uint32_t)z * 83492791u)) & mask;
+}
+
+__host__ __device__ __forceinline__ unsigned long long pack_key(int x, int y, int z)
+{
+    return (unsigned long long)(uint16_t)x | ((unsigned long long)(uint16_t)y << 16) |
+           ((unsigned long long)(uint16_t)z << 32) | (1ull << 48);
+}
+
+__device__ __forceinline__ void unpack_key(unsigned long long k, int &x, int &y, int &z)
+{
+    x = (int)(int16_t)(k & 0xffff);
+    y = (int)(int16_t)((k >> 16) & 0xffff);
+    z = (int)(int16_t)((k >> 32) & 0xffff);
+}
+
+__device__ __forceinline__ unsigned long long entry_key(const int4 &e)
+{
+    return (unsigned long long)(uint32_t)e.x | ((unsigned long long)(uint32_t)e.y << 32);
+}
+
+// Sec. 3.3 retrieval through the read-only path (tables not modified by the
+// running kernel).  Returns the block index or -1.
+__device__ __forceinline__ int lookup_ro(const SceneDev &s, int bx, int by, int bz)
+{
+    const unsigned long long key = pack_key(bx, by, bz);
+    int idx = (int)hash_bucket(bx, by, bz, (uint32_t)(s.nb - 1));
+    const int4 *E = reinterpret_cast<const int4 *>(s.entries);
+    for (int guard = 0; guard <= s.ne; ++guard) {
+        int4 e = __ldg(&E[idx]);
+        if (entry_key(e) == key && e.w >= 0) return e.w;
+        if (e.z < 1) return -1;
+        idx = s.nb + e.z - 1;
+    }
+    return -1;
+}
+
+// Same, through L2 (coherent with writes made earlier by the same kernel).
+__device__ __forceinline__ int lookup_cg(const SceneDev &s, int bx, int by, int bz)
+{
+    const unsigned long long key = pack_key(bx, by, bz);
+    int idx = (int)hash_bucket(bx, by, bz, (uint32_t)(s.nb - 1));
+    const int4 *E = reinterpret_cast<const int4 *>(s.entries);
+    for (int guard = 0; guard <= s.ne; ++guard) {
+        int4 e = __ldcg(&E[idx]);
+        if (entry_key(e) == key && e.w >= 0) return e.w;
+        if (e.z < 1) return -1;
+        idx = s.nb + e.z - 1;
+    }
+    return -1;
+}
+
+// ------------------------------------------------ IEEE round-to-nearest ops
+// Every operation that decides an integer (which block, which pixel, whether
+// a voxel is updated) is written with these so that no multiply-add is fused.
+__device__ __forceinline__ float fadd(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float fsub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float fmul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fdiv(float a, float b) { return __fdiv_rn(a, b); }
+
+// ((m0 x + m1 y) + m2 z) + m3, each operation rounded on its own.
+__device__ __forceinline__ float row_apply(const float *m, float x, float y, float z)
+{
+    return fadd(fadd(fadd(fmul(m[0], x), fmul(m[1], y)), fmul(m[2], z)), m[3]);
+}
+
+// --------------------------------------------------------------- atomics
+
+__device__ __forceinline__ void set_status(const SceneDev &s, uint32_t bits)
+{
+    atomicOr(&s.ctr->status, bits);
+}
+
+// Warp-aggregated append: the lanes active at the call each get a distinct
+// slot; one atomic per warp.
+__device__ __forceinline__ int warp_append(int32_t *counter)
+{
+    const unsigned m = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(counter, __popc(m));
+    base = __shfl_sync(m, base, leader);
+    return base + __popc(m & ((1u << lane) - 1u));
+}
+
+}  // namespace itm
+
+// Opaque handle behind the C ABI.
+struct itm_scene {
+    itm_scene_params params;
+    itm::SceneDev d;
+    cudaStream_t last_stream;
+    int device;
+};
+
+// Host helpers implemented in itm_scene.cu.
+namespace itm {
+int check_cuda(cudaError_t e);
+void pose_rows(const float T[16], Mat34 &out);        // rows 0..2 of T
+void rigid_inverse_rows(const float T[16], Mat34 &out); // rows 0..2 of T^-1 (fp64, rounded once)
+int valid_intr(const itm_intrinsics *in);
+Intr to_intr(const itm_intrinsics *in);
+}  // namespace itm
+
+// Launchers implemented in the kernel translation units.
+namespace itm {
+cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &in, const Mat34 &T_wc,
+                            const Mat34 &M_d, cudaStream_t st);
+cudaError_t launch_integrate(const SceneDev &s, const float *depth, const float *wpx, const Intr &in,
+                             const Mat34 &M_d, cudaStream_t st);
+cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, float4 *vtx, float4 *nrm,
+                           cudaStream_t st);
+cudaError_t launch_depth_u16(const uint16_t *raw, float *out, int64_t n, cudaStream_t st);
+cudaError_t launch_reset(const SceneDev &s, cudaStream_t st);
+}  // namespace itm

@@ -1,0 +1,427 @@
+// Host side of the C ABI: scene lifetime, argument checks, pose algebra,
+// per-frame entry points, counters, export / import of the volume.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "itm_internal.cuh"
+
+namespace itm {
+
+int overflow_capacity();  // itm_alloc.cu
+
+int check_cuda(cudaError_t e) { return e == cudaSuccess ? ITM_OK : ITM_ERR_CUDA; }
+
+void pose_rows(const float T[16], Mat34 &out)
+{
+    for (int i = 0; i < 12; ++i) out.m[i] = T[i];
+}
+
+// Rows 0..2 of T^-1 for a rigid T = [R t]: [R^T, -R^T t], evaluated in double
+// (the translation accumulated as 0 - r0 t0 - r1 t1 - r2 t2) and rounded once.
+void rigid_inverse_rows(const float T[16], Mat34 &out)
+{
+    double R[3][3], t[3];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) R[i][j] = (double)T[4 * i + j];
+        t[i] = (double)T[4 * i + 3];
+    }
+    for (int i = 0; i < 3; ++i) {
+        double acc = 0.0;
+        for (int j = 0; j < 3; ++j) {
+            out.m[4 * i + j] = (float)R[j][i];
+            acc -= R[j][i] * t[j];
+        }
+        out.m[4 * i + 3] = (float)acc;
+    }
+}
+
+int valid_intr(const itm_intrinsics *in)
+{
+    return in && in->width > 2 && in->height > 2 && in->width <= 32768 && in->height <= 32768 && in->fx > 0.0f &&
+           in->fy > 0.0f && isfinite(in->fx) && isfinite(in->fy) && isfinite(in->cx) && isfinite(in->cy) &&
+           (long long)in->width * in->height < (1ll << 30);
+}
+
+static int valid_pose(const float *T)
+{
+    if (!T) return 0;
+    for (int i = 0; i < 16; ++i)
+        if (!isfinite(T[i])) return 0;
+    return 1;
+}
+
+Intr to_intr(const itm_intrinsics *in)
+{
+    Intr r;
+    r.W = in->width;
+    r.H = in->height;
+    r.fx = in->fx;
+    r.fy = in->fy;
+    r.cx = in->cx;
+    r.cy = in->cy;
+    return r;
+}
+
+static int valid_params(const itm_scene_params *p)
+{
+    if (!p) return 0;
+    if (!(p->voxel_size > 0.0f) || !(p->mu > 0.0f)) return 0;
+    if (p->weight_mode != 0 && p->weight_mode != 1) return 0;
+    if (p->max_w < 1 || (p->weight_mode == 0 && p->max_w > 255)) return 0;
+    if (p->num_buckets < 1 || p->num_buckets > (1 << 30) || (p->num_buckets & (p->num_buckets - 1))) return 0;
+    if (p->num_excess < 0 || p->num_excess > (1 << 28)) return 0;
+    if (p->num_blocks < 0 || p->num_blocks > (1 << 24)) return 0;
+    if (!(p->z_min > 0.0f) || !(p->z_max > p->z_min)) return 0;
+    return 1;
+}
+
+static void free_dev(SceneDev &d)
+{
+    void *ptrs[] = {d.entries, d.req, d.req_list, d.overflow, d.visible, d.block_pos, d.sdf,
+                    d.w8, d.w32, d.block_free, d.excess_free, d.ctr};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    memset(&d, 0, sizeof(d));
+}
+
+static const char kVersion[] = "itm-gb300 0.1 (sm_103a)";
+
+}  // namespace itm
+
+using namespace itm;
+
+extern "C" {
+
+const char *itm_version(void) { return kVersion; }
+
+uint32_t itm_hash_index(int x, int y, int z, int num_buckets)
+{
+    return hash_bucket(x, y, z, (uint32_t)(num_buckets - 1));
+}
+
+int itm_scene_create(const itm_scene_params *params, itm_scene **out)
+{
+    if (!out || !valid_params(params)) return ITM_ERR_ARG;
+    *out = nullptr;
+    itm_scene *sc = (itm_scene *)calloc(1, sizeof(itm_scene));
+    if (!sc) return ITM_ERR_ARG;
+    sc->params = *params;
+    cudaGetDevice(&sc->device);
+    SceneDev &d = sc->d;
+    d.nb = params->num_buckets;
+    d.ne = params->num_excess;
+    d.nv = params->num_blocks;
+    d.ovf_cap = overflow_capacity();
+    d.voxel_size = params->voxel_size;
+    d.mu = params->mu;
+    d.z_min = params->z_min;
+    d.z_max = params->z_max;
+    d.max_w = params->max_w;
+    d.weight_mode = params->weight_mode;
+    const size_t nvox = (size_t)d.nv * kBlockVoxels;
+    cudaError_t e = cudaSuccess;
+#define ITM_ALLOC(ptr, bytes)                                         \
+    if (e == cudaSuccess) e = cudaMalloc((void **)&(ptr), (bytes) > 0 ? (bytes) : 16);
+    ITM_ALLOC(d.entries, sizeof(Entry) * (size_t)(d.nb + d.ne));
+    ITM_ALLOC(d.req, sizeof(unsigned long long) * (size_t)d.nb);
+    ITM_ALLOC(d.req_list, sizeof(int32_t) * (size_t)d.nb);
+    ITM_ALLOC(d.overflow, sizeof(unsigned long long) * (size_t)d.ovf_cap);
+    ITM_ALLOC(d.visible, sizeof(int32_t) * (size_t)(d.nv > 0 ? d.nv : 1));
+    ITM_ALLOC(d.block_pos, sizeof(short4) * (size_t)(d.nv > 0 ? d.nv : 1));
+    ITM_ALLOC(d.sdf, sizeof(float) * nvox);
+    if (d.weight_mode == 0) {
+        ITM_ALLOC(d.w8, nvox);
+    } else {
+        ITM_ALLOC(d.w32, sizeof(float) * nvox);
+    }
+    ITM_ALLOC(d.block_free, sizeof(int32_t) * (size_t)(d.nv > 0 ? d.nv : 1));
+    ITM_ALLOC(d.excess_free, sizeof(int32_t) * (size_t)(d.ne > 0 ? d.ne : 1));
+    ITM_ALLOC(d.ctr, sizeof(Counters));
+#undef ITM_ALLOC
+    if (e == cudaSuccess) e = launch_reset(d, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+        free_dev(d);
+        free(sc);
+        cudaGetLastError();
+        return ITM_ERR_CUDA;
+    }
+    sc->last_stream = 0;
+    *out = sc;
+    return ITM_OK;
+}
+
+int itm_scene_destroy(itm_scene *sc)
+{
+    if (!sc) return ITM_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_dev(sc->d);
+    free(sc);
+    return ITM_OK;
+}
+
+int itm_scene_reset(itm_scene *sc, itm_stream stream)
+{
+    if (!sc) return ITM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    sc->last_stream = st;
+    return check_cuda(launch_reset(sc->d, st));
+}
+
+int itm_allocate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
+                 itm_stream stream)
+{
+    if (!sc || !depth_dev || !valid_pose(T_wc) || !valid_intr(intr)) return ITM_ERR_ARG;
+    Mat34 T, M;
+    pose_rows(T_wc, T);
+    rigid_inverse_rows(T_wc, M);
+    cudaStream_t st = (cudaStream_t)stream;
+    sc->last_stream = st;
+    return check_cuda(launch_allocate(sc->d, depth_dev, to_intr(intr), T, M, st));
+}
+
+int itm_integrate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
+                  itm_stream stream)
+{
+    if (!sc || !depth_dev || !valid_pose(T_wc) || !valid_intr(intr)) return ITM_ERR_ARG;
+    if (sc->d.weight_mode != 0) return ITM_ERR_ARG;
+    Mat34 M;
+    rigid_inverse_rows(T_wc, M);
+    cudaStream_t st = (cudaStream_t)stream;
+    sc->last_stream = st;
+    return check_cuda(launch_integrate(sc->d, depth_dev, nullptr, to_intr(intr), M, st));
+}
+
+int itm_integrate_weighted(itm_scene *sc, const float *depth_dev, const float *wpx_dev, const itm_intrinsics *intr,
+                           const float T_wc[16], itm_stream stream)
+{
+    if (!sc || !depth_dev || !wpx_dev || !valid_pose(T_wc) || !valid_intr(intr)) return ITM_ERR_ARG;
+    if (sc->d.weight_mode != 1) return ITM_ERR_ARG;
+    Mat34 M;
+    rigid_inverse_rows(T_wc, M);
+    cudaStream_t st = (cudaStream_t)stream;
+    sc->last_stream = st;
+    return check_cuda(launch_integrate(sc->d, depth_dev, wpx_dev, to_intr(intr), M, st));
+}
+
+int itm_raycast(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16], float *vertex_dev,
+                float *normal_dev, itm_stream stream)
+{
+    if (!sc || !valid_pose(T_wc) || !vertex_dev || !normal_dev || !valid_intr(intr)) return ITM_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(vertex_dev) & 15) || (reinterpret_cast<uintptr_t>(normal_dev) & 15))
+        return ITM_ERR_ARG;
+    Mat34 T;
+    pose_rows(T_wc, T);
+    cudaStream_t st = (cudaStream_t)stream;
+    sc->last_stream = st;
+    return check_cuda(launch_raycast(sc->d, to_intr(intr), T, reinterpret_cast<float4 *>(vertex_dev),
+                                     reinterpret_cast<float4 *>(normal_dev), st));
+}
+
+int itm_process_frame(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
+                      float *vertex_dev, float *normal_dev, itm_stream stream)
+{
+    if (!sc || (vertex_dev && !normal_dev)) return ITM_ERR_ARG;
+    int r = itm_allocate(sc, depth_dev, intr, T_wc, stream);
+    if (r == ITM_OK) r = itm_integrate(sc, depth_dev, intr, T_wc, stream);
+    if (r == ITM_OK && vertex_dev) r = itm_raycast(sc, intr, T_wc, vertex_dev, normal_dev, stream);
+    return r;
+}
+
+int itm_depth_u16_to_f32(const uint16_t *raw_dev, float *depth_dev, int64_t n, itm_stream stream)
+{
+    if (n < 0 || (n > 0 && (!raw_dev || !depth_dev))) return ITM_ERR_ARG;
+    return check_cuda(launch_depth_u16(raw_dev, depth_dev, n, (cudaStream_t)stream));
+}
+
+int itm_scene_stats(itm_scene *sc, itm_stats *out)
+{
+    if (!sc || !out) return ITM_ERR_ARG;
+    Counters c;
+    cudaError_t e = cudaStreamSynchronize(sc->last_stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&c, sc->d.ctr, sizeof(c), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ITM_ERR_CUDA;
+    out->status = c.status;
+    out->allocated_blocks = c.block_head < sc->d.nv ? c.block_head : sc->d.nv;
+    out->excess_used = c.excess_head < sc->d.ne ? c.excess_head : sc->d.ne;
+    out->visible_blocks = c.n_visible;
+    out->last_requests = c.n_req;
+    out->last_overflow = c.n_overflow;
+    out->updated_voxels = c.updated;
+    out->visited_voxels = c.visited;
+    out->frames = c.frames;
+    return ITM_OK;
+}
+
+int itm_scene_status(itm_scene *sc)
+{
+    itm_stats st;
+    int r = itm_scene_stats(sc, &st);
+    if (r != ITM_OK) return r;
+    if (st.status & ITM_ST_HASH_FULL) return ITM_ERR_HASH_FULL;
+    if (st.status & ITM_ST_VBA_FULL) return ITM_ERR_VBA_FULL;
+    if (st.status & ITM_ST_RANGE) return ITM_ERR_RANGE;
+    if (st.status & ITM_ST_TIMEOUT) return ITM_ERR_TIMEOUT;
+    if (st.status & ITM_ST_OVERFLOW) return ITM_ERR_OVERFLOW;
+    return ITM_OK;
+}
+
+// Blocks are handed out from the free list front to back and never returned,
+// so the allocated blocks are the list's first min(block_head, nv) indices;
+// at reset the list is the identity, so they are block indices 0 .. n-1.
+int itm_scene_export(itm_scene *sc, int16_t *coords_host, float *sdf_host, float *w_host, int cap, int *n)
+{
+    if (!sc || !n || cap < 0 || (cap > 0 && !coords_host)) return ITM_ERR_ARG;
+    itm_stats st;
+    int r = itm_scene_stats(sc, &st);
+    if (r != ITM_OK) return r;
+    const int total = st.allocated_blocks;
+    std::vector<short4> pos((size_t)(total > 0 ? total : 1));
+    std::vector<int32_t> order((size_t)(total > 0 ? total : 1));
+    cudaError_t e = cudaSuccess;
+    if (total > 0) {
+        e = cudaMemcpy(order.data(), sc->d.block_free, sizeof(int32_t) * total, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(pos.data(), sc->d.block_pos, sizeof(short4) * total, cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return ITM_ERR_CUDA;
+    for (int i = 0; i < total; ++i)
+        if (order[i] != i) return ITM_ERR_ARG;  // the front-to-back invariant above
+    int k = 0;
+    std::vector<int> keep;
+    keep.reserve(total);
+    for (int i = 0; i < total; ++i)
+        if (pos[i].w) keep.push_back(i);
+    const int m = (int)keep.size();
+    *n = m;
+    const int cnt = m < cap ? m : cap;
+    std::vector<float> sdf, wf;
+    std::vector<uint8_t> w8;
+    if (cnt > 0 && (sdf_host || w_host)) {
+        const size_t nvox = (size_t)total * kBlockVoxels;
+        if (sdf_host) {
+            sdf.resize(nvox);
+            e = cudaMemcpy(sdf.data(), sc->d.sdf, sizeof(float) * nvox, cudaMemcpyDeviceToHost);
+        }
+        if (e == cudaSuccess && w_host) {
+            if (sc->d.weight_mode == 0) {
+                w8.resize(nvox);
+                e = cudaMemcpy(w8.data(), sc->d.w8, nvox, cudaMemcpyDeviceToHost);
+            } else {
+                wf.resize(nvox);
+                e = cudaMemcpy(wf.data(), sc->d.w32, sizeof(float) * nvox, cudaMemcpyDeviceToHost);
+            }
+        }
+        if (e != cudaSuccess) return ITM_ERR_CUDA;
+    }
+    for (k = 0; k < cnt; ++k) {
+        const int b = keep[k];
+        coords_host[3 * k + 0] = pos[b].x;
+        coords_host[3 * k + 1] = pos[b].y;
+        coords_host[3 * k + 2] = pos[b].z;
+        if (sdf_host) memcpy(&sdf_host[(size_t)k * kBlockVoxels], &sdf[(size_t)b * kBlockVoxels], sizeof(float) * kBlockVoxels);
+        if (w_host) {
+            for (int i = 0; i < kBlockVoxels; ++i)
+                w_host[(size_t)k * kBlockVoxels + i] = sc->d.weight_mode == 0 ? (float)w8[(size_t)b * kBlockVoxels + i]
+                                                                              : wf[(size_t)b * kBlockVoxels + i];
+        }
+    }
+    return ITM_OK;
+}
+
+int itm_scene_export_table(itm_scene *sc, int32_t *entries_host)
+{
+    if (!sc || !entries_host) return ITM_ERR_ARG;
+    const size_t total = (size_t)sc->d.nb + sc->d.ne;
+    std::vector<Entry> E(total);
+    cudaError_t e = cudaStreamSynchronize(sc->last_stream);
+    if (e == cudaSuccess) e = cudaMemcpy(E.data(), sc->d.entries, sizeof(Entry) * total, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ITM_ERR_CUDA;
+    for (size_t i = 0; i < total; ++i) {
+        entries_host[5 * i + 0] = E[i].x;
+        entries_host[5 * i + 1] = E[i].y;
+        entries_host[5 * i + 2] = E[i].z;
+        entries_host[5 * i + 3] = E[i].offset;
+        entries_host[5 * i + 4] = E[i].flag ? E[i].ptr : -2;
+    }
+    return ITM_OK;
+}
+
+int itm_scene_import(itm_scene *sc, const int16_t *coords_host, const float *sdf_host, const float *w_host, int n)
+{
+    if (!sc || n < 0 || n > sc->d.nv || (n > 0 && (!coords_host || !sdf_host || !w_host))) return ITM_ERR_ARG;
+    const SceneDev &d = sc->d;
+    // Sec. 3.3 insertion, sequentially on the host: bucket first, then the
+    // excess chain; block i of the input becomes block index i.
+    std::vector<Entry> E((size_t)d.nb + d.ne);
+    for (auto &x : E) {
+        memset(&x, 0, sizeof(x));
+        x.ptr = -2;
+    }
+    int used_excess = 0;
+    std::vector<short4> pos((size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+        const int x = coords_host[3 * i], y = coords_host[3 * i + 1], z = coords_host[3 * i + 2];
+        const uint32_t h = hash_bucket(x, y, z, (uint32_t)(d.nb - 1));
+        Entry *e = &E[h];
+        Entry fresh;
+        fresh.x = (int16_t)x;
+        fresh.y = (int16_t)y;
+        fresh.z = (int16_t)z;
+        fresh.flag = 1;
+        fresh.offset = 0;
+        fresh.ptr = i;
+        pos[i] = make_short4((short)x, (short)y, (short)z, 1);
+        if (!e->flag) {
+            *e = fresh;
+            continue;
+        }
+        for (;;) {
+            if (e->x == x && e->y == y && e->z == z) return ITM_ERR_ARG;  // duplicate
+            if (e->offset < 1) break;
+            e = &E[(size_t)d.nb + e->offset - 1];
+        }
+        if (used_excess >= d.ne) return ITM_ERR_HASH_FULL;
+        E[(size_t)d.nb + used_excess] = fresh;
+        e->offset = used_excess + 1;
+        ++used_excess;
+    }
+    const size_t nvox = (size_t)n * kBlockVoxels;
+    std::vector<uint8_t> w8;
+    if (d.weight_mode == 0 && n > 0) {
+        w8.resize(nvox);
+        for (size_t i = 0; i < nvox; ++i) {
+            const float w = w_host[i];
+            if (!(w >= 0.0f && w <= (float)d.max_w) || w != (float)(int)w) return ITM_ERR_ARG;
+            w8[i] = (uint8_t)w;
+        }
+    }
+    cudaError_t e = cudaStreamSynchronize(sc->last_stream);
+    if (e == cudaSuccess) e = launch_reset(d, 0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e == cudaSuccess)
+        e = cudaMemcpy(d.entries, E.data(), sizeof(Entry) * E.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && n > 0) {
+        e = cudaMemcpy(d.block_pos, pos.data(), sizeof(short4) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpy(d.sdf, sdf_host, sizeof(float) * nvox, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            if (d.weight_mode == 0) e = cudaMemcpy(d.w8, w8.data(), nvox, cudaMemcpyHostToDevice);
+            else e = cudaMemcpy(d.w32, w_host, sizeof(float) * nvox, cudaMemcpyHostToDevice);
+        }
+    }
+    if (e == cudaSuccess) {
+        Counters c;
+        memset(&c, 0, sizeof(c));
+        c.block_head = n;
+        c.excess_head = used_excess;
+        e = cudaMemcpy(d.ctr, &c, sizeof(c), cudaMemcpyHostToDevice);
+    }
+    sc->last_stream = 0;
+    return check_cuda(e);
+}
+
+}  // extern "C"

@@ -1,0 +1,59 @@
+"""The C ABI library loads and exports every function the header declares.
+No GPU calls: only symbol presence and the host-side hash function."""
+
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    text = open(os.path.join(ROOT, "include", "itm.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(itm_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libitm():
+    import __graft_entry__
+    path = __graft_entry__._build_module().build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_core_calls():
+    fns = header_functions()
+    for name in ("itm_scene_create", "itm_allocate", "itm_integrate", "itm_raycast", "itm_scene_destroy"):
+        assert name in fns
+
+
+def test_library_exports_every_declared_symbol(libitm):
+    missing = [f for f in header_functions() if not hasattr(libitm, f)]
+    assert not missing, missing
+
+
+def test_binding_names_match_header():
+    import paper_1708_00783_gb300 as itm
+    for f in header_functions():
+        assert callable(getattr(itm, f, None)), f
+
+
+def test_host_hash_index_follows_printed_function():
+    """Sec. 3.2 primes, unsigned wrap-around, mask by buckets - 1 (the values
+    come from the paper's printed constants, not from the oracle)."""
+    import paper_1708_00783_gb300 as itm
+    from tests.test_oracle_pins import golden
+    g = golden("hash_function.txt")
+    nb = 1 << 30
+    assert itm.itm_hash_index(1, 0, 0, nb) == g["prime_x"] % nb
+    assert itm.itm_hash_index(0, 1, 0, nb) == g["prime_y"] % nb
+    assert itm.itm_hash_index(0, 0, 1, nb) == g["prime_z"] % nb
+    assert itm.itm_hash_index(-1, -1, -1, 1 << 20) == (
+        ((1 << 32) - g["prime_x"]) ^ ((1 << 32) - g["prime_y"]) ^ ((1 << 32) - g["prime_z"])) % (1 << 20)
+
+
+def test_version_string():
+    import paper_1708_00783_gb300 as itm
+    assert "sm_103a" in itm.itm_version()
