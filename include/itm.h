@@ -49,6 +49,7 @@ enum {
     ITM_ERR_RANGE = 5,     /* status: block coordinate outside int16 */
     ITM_ERR_TIMEOUT = 6,   /* status: a bounded device-side wait gave up */
     ITM_ERR_OVERFLOW = 7,  /* status: a per-frame work list overflowed */
+    ITM_ERR_TOO_LARGE = 8, /* the input could exceed a fixed-size buffer of the call */
 };
 
 /* Sticky status bits (itm_stats.status). */
@@ -198,6 +199,42 @@ uint32_t itm_hash_index(int x, int y, int z, int num_buckets);
 
 /* Library version string. */
 const char *itm_version(void);
+
+/* Distinct blocks one itm_frame_blocks_noalloc call can hold. */
+#define ITM_NOALLOC_MAX_BLOCKS (1 << 21)
+
+/* The voxel blocks one depth frame touches, computed without allocating
+ * memory.  The paper has no counterpart: this serves callers that cannot
+ * call cudaMalloc once they are running -- a real-time loop that must not
+ * wait on the allocator, a host framework whose device memory comes only
+ * from its own fixed arenas, a system that forbids dynamic allocation after
+ * start-up -- but want to know which blocks a frame needs (to reserve or
+ * stream storage of their own).  It needs no scene.
+ *
+ * Result: the set of blocks that itm_allocate would insert into an empty
+ * scene with these parameters (the segment d - mu .. d + mu of every pixel
+ * with z_min <= d <= z_max, every block crossed), in no particular order, as
+ * int16 (x, y, z) triples in coords_dev (caller device memory, cap triples);
+ * *count_dev (caller device memory) receives the number of distinct blocks,
+ * which may exceed cap (then only cap are written).  A negative count means
+ * the fixed set overflowed (excluded by the size check below).
+ *
+ * Memory: the de-duplication set is a fixed device array of
+ * 2 * ITM_NOALLOC_MAX_BLOCKS 64-bit words (32 MiB) inside the library,
+ * present on every GPU that loads the library until the process exits.
+ * The first call on a device looks up that array's address (with the
+ * device current); make that first call before any stream capture.  Each
+ * call clears the array and the count before use.  All calls share the
+ * array: calls that overlap on the GPU (other streams, other host threads)
+ * race and give wrong results.
+ *
+ * Errors: ITM_ERR_ARG for null pointers, invalid intrinsics, parameters or
+ * a non-finite pose; ITM_ERR_TOO_LARGE when width * height * (the most
+ * blocks one pixel's segment can cross) exceeds ITM_NOALLOC_MAX_BLOCKS;
+ * ITM_ERR_CUDA when a CUDA call fails.  Asynchronous on `stream`. */
+int itm_frame_blocks_noalloc(const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
+                             float voxel_size, float mu, float z_min, float z_max, int16_t *coords_dev,
+                             int cap, int32_t *count_dev, itm_stream stream);
 
 #ifdef __cplusplus
 }

@@ -21,7 +21,8 @@ LIB_PATH = _build_mod.LIB
 
 ITM_OK = 0
 ERRORS = {1: "ITM_ERR_ARG", 2: "ITM_ERR_CUDA", 3: "ITM_ERR_HASH_FULL", 4: "ITM_ERR_VBA_FULL",
-          5: "ITM_ERR_RANGE", 6: "ITM_ERR_TIMEOUT", 7: "ITM_ERR_OVERFLOW"}
+          5: "ITM_ERR_RANGE", 6: "ITM_ERR_TIMEOUT", 7: "ITM_ERR_OVERFLOW", 8: "ITM_ERR_TOO_LARGE"}
+ITM_NOALLOC_MAX_BLOCKS = 1 << 21
 ST_HASH_FULL, ST_VBA_FULL, ST_RANGE, ST_TIMEOUT, ST_OVERFLOW = 0x1, 0x2, 0x4, 0x8, 0x10
 
 
@@ -57,7 +58,7 @@ EXPORTED = [
     "itm_scene_create", "itm_scene_destroy", "itm_scene_reset", "itm_allocate", "itm_integrate",
     "itm_integrate_weighted", "itm_raycast", "itm_process_frame", "itm_depth_u16_to_f32",
     "itm_scene_stats", "itm_scene_status", "itm_scene_export", "itm_scene_export_table",
-    "itm_scene_import", "itm_hash_index", "itm_version",
+    "itm_scene_import", "itm_hash_index", "itm_version", "itm_frame_blocks_noalloc",
 ]
 
 
@@ -86,6 +87,7 @@ def _load():
         "itm_scene_import": (I, [P, P, P, P, I]),
         "itm_hash_index": (ctypes.c_uint32, [I, I, I, I]),
         "itm_version": (ctypes.c_char_p, []),
+        "itm_frame_blocks_noalloc": (I, [P, ip, fp16, F, F, F, F, P, I, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -239,6 +241,15 @@ def itm_hash_index(x, y, z, num_buckets) -> int:
 
 def itm_version() -> str:
     return _lib.itm_version().decode()
+
+
+def itm_frame_blocks_noalloc(depth, intr, T_wc, voxel_size, mu, z_min, z_max, coords, cap, count, stream=None):
+    """Blocks one depth frame touches, into caller buffers (coords: device
+    int16 [cap, 3]; count: device int32 [1]); the library allocates nothing."""
+    a, p = _pose(T_wc)
+    _check(_lib.itm_frame_blocks_noalloc(_ptr(depth), ctypes.byref(intr), p, float(voxel_size), float(mu),
+                                         float(z_min), float(z_max), _ptr(coords), int(cap), _ptr(count),
+                                         _stream(stream)), "itm_frame_blocks_noalloc")
 
 
 # ------------------------------------------------------------ convenience

@@ -33,6 +33,7 @@ SOURCES = {
     "itm_integrate.cu": ["-fmad=false"],
     "itm_raycast.cu": ["-fmad=false"],
     "itm_depth.cu": ["-fmad=false"],
+    "itm_noalloc.cu": ["-fmad=false"],
 }
 
 

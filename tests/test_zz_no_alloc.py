@@ -1,0 +1,78 @@
+"""The allocation-free block query against the scene path.
+
+itm_frame_blocks_noalloc serves callers that cannot allocate device memory
+once they are running (a real-time loop that must not wait on the
+allocator, a framework that hands out device memory only from its own fixed
+arenas).  It must return exactly the blocks that itm_allocate inserts into an
+empty scene.  Consecutive calls share the library's fixed set, so the calls
+below run back to back on overlapping frames: a set not cleared between
+calls would hide blocks of the second frame.
+"""
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _intr(itm, w):
+    return itm.make_intrinsics(w.intr.width, w.intr.height, w.intr.fx, w.intr.fy, w.intr.cx, w.intr.cy)
+
+
+def test_noalloc_block_set_equals_scene_allocation_on_consecutive_calls():
+    import torch
+
+    import paper_1708_00783_gb300 as itm
+    from synth import kinect_workload, tiny_workload
+
+    cap = 1 << 20
+    coords = torch.empty((cap, 3), dtype=torch.int16, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    kinect = kinect_workload()
+    calls = [(tiny_workload(n_frames=2), 1), (kinect, 5), (kinect, 6)]
+    for w, k in calls:
+        f = w.frame(k)
+        d = _dev(f.depth)
+        ci = _intr(itm, w)
+        p = w.params
+        itm.itm_frame_blocks_noalloc(d, ci, f.T_wc, p["voxel_size"], p["mu"], p["z_min"], p["z_max"],
+                                     coords, cap, count)
+        torch.cuda.synchronize()
+        n = int(count.item())
+        assert 0 < n <= cap
+        got = coords[:n].cpu().numpy()
+        got_set = {tuple(c) for c in got.tolist()}
+        assert len(got_set) == n, "a block was reported twice"
+        ref = itm.Scene(**p)
+        ref.allocate(d, ci, f.T_wc)
+        want = {tuple(c) for c in ref.export(with_voxels=False)[0].tolist()}
+        assert ref.status() == 0
+        assert got_set == want, (len(got_set - want), len(want - got_set))
+        ref.close()
+
+
+def test_noalloc_rejects_inputs_beyond_its_fixed_set():
+    import torch
+
+    import paper_1708_00783_gb300 as itm
+
+    W, H = 4096, 4096
+    depth = torch.ones((H, W), dtype=torch.float32, device="cuda")
+    coords = torch.empty((16, 3), dtype=torch.int16, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ci = itm.make_intrinsics(W, H, 500.0, 500.0, W / 2, H / 2)
+    with pytest.raises(itm.ItmError) as e:
+        itm.itm_frame_blocks_noalloc(depth, ci, np.eye(4), 0.005, 0.02, 0.4, 5.0, coords, 16, count)
+    assert e.value.code == 8  # ITM_ERR_TOO_LARGE
+    # a small cap is fine: the count still reports every block
+    w = 64
+    small = torch.ones((w, w), dtype=torch.float32, device="cuda")
+    cs = itm.make_intrinsics(w, w, 60.0, 60.0, w / 2, w / 2)
+    itm.itm_frame_blocks_noalloc(small, cs, np.eye(4), 0.005, 0.02, 0.4, 5.0, coords, 16, count)
+    torch.cuda.synchronize()
+    assert int(count.item()) > 16
