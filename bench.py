@@ -427,7 +427,7 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": 7 * args.steps,
+        "gpu_launches": 8 * args.steps,  # u16, enumerate, commit, overflow, visible, integrate, range, raycast
     }
     print(json.dumps(line), flush=True)
 

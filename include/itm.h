@@ -157,6 +157,18 @@ int itm_integrate_weighted(itm_scene *scene, const float *depth_dev, const float
 int itm_raycast(itm_scene *scene, const itm_intrinsics *intr, const float T_wc[16],
                 float *vertex_dev, float *normal_dev, itm_stream stream);
 
+/* Sec. 4.4 search range, per 8x4-pixel tile (tile (i, j) covers pixels
+ * u = 8i .. 8i+7, v = 4j .. 4j+3; ceil(width/8) x ceil(height/4) tiles,
+ * row-major): the nearest and farthest camera depth of the allocated blocks
+ * that can cover the tile, each block taken as the region of points whose
+ * nearest voxel it holds, clipped to z >= z_min, with small margins.  A tile
+ * no block covers gets zmin = NaN (all bits set) and zmax = 0.  zmin_dev,
+ * zmax_dev: device float[tiles].  itm_raycast computes the same range
+ * internally (for images up to 4096 x 4096) and uses it only to skip hash
+ * probes it can prove unallocated; its result does not depend on it. */
+int itm_raycast_range(itm_scene *scene, const itm_intrinsics *intr, const float T_wc[16], float *zmin_dev,
+                      float *zmax_dev, itm_stream stream);
+
 /* One frame of the per-frame core: itm_allocate, itm_integrate and (when
  * vertex_dev is not NULL) itm_raycast, on one stream. */
 int itm_process_frame(itm_scene *scene, const float *depth_dev, const itm_intrinsics *intr,

@@ -58,7 +58,7 @@ EXPORTED = [
     "itm_scene_create", "itm_scene_destroy", "itm_scene_reset", "itm_allocate", "itm_integrate",
     "itm_integrate_weighted", "itm_raycast", "itm_process_frame", "itm_depth_u16_to_f32",
     "itm_scene_stats", "itm_scene_status", "itm_scene_export", "itm_scene_export_table",
-    "itm_scene_import", "itm_hash_index", "itm_version", "itm_frame_blocks_noalloc",
+    "itm_scene_import", "itm_hash_index", "itm_version", "itm_frame_blocks_noalloc", "itm_raycast_range",
 ]
 
 
@@ -88,6 +88,7 @@ def _load():
         "itm_hash_index": (ctypes.c_uint32, [I, I, I, I]),
         "itm_version": (ctypes.c_char_p, []),
         "itm_frame_blocks_noalloc": (I, [P, ip, fp16, F, F, F, F, P, I, P, P]),
+        "itm_raycast_range": (I, [P, ip, fp16, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -182,6 +183,12 @@ def itm_raycast(scene, intr, T_wc, vertex, normal, stream=None):
     a, p = _pose(T_wc)
     _check(_lib.itm_raycast(scene, ctypes.byref(intr), p, _ptr(vertex), _ptr(normal), _stream(stream)),
            "itm_raycast")
+
+
+def itm_raycast_range(scene, intr, T_wc, zmin, zmax, stream=None):
+    a, p = _pose(T_wc)
+    _check(_lib.itm_raycast_range(scene, ctypes.byref(intr), p, _ptr(zmin), _ptr(zmax), _stream(stream)),
+           "itm_raycast_range")
 
 
 def itm_process_frame(scene, depth, intr, T_wc, vertex=None, normal=None, stream=None):

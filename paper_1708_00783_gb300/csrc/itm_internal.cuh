@@ -22,6 +22,9 @@
 namespace itm {
 
 constexpr int kBlockVoxels = 512;
+// largest image whose raycast uses the search-range tiles (8x4 pixels each)
+constexpr int kRangeMaxW = 4096, kRangeMaxH = 4096;
+constexpr int kRangeMaxTiles = (kRangeMaxW / 8) * (kRangeMaxH / 4);
 constexpr unsigned kFull = 0xffffffffu;
 
 // Sec. 3.2 hash entry.  Bytes 0..7 (x, y, z, flag) form the packed block key
@@ -64,6 +67,8 @@ struct SceneDev {
     int32_t *block_free;
     int32_t *excess_free;
     Counters *ctr;
+    uint32_t *range_min;  // per 8x4 tile: nearest / farthest depth (float bits) of covering blocks
+    uint32_t *range_max;
     int nb, ne, nv;
     int ovf_cap;
     float voxel_size, mu, z_min, z_max;
@@ -196,8 +201,11 @@ cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &i
                             const Mat34 &M_d, cudaStream_t st);
 cudaError_t launch_integrate(const SceneDev &s, const float *depth, const float *wpx, const Intr &in,
                              const Mat34 &M_d, cudaStream_t st);
-cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, float4 *vtx, float4 *nrm,
-                           cudaStream_t st);
+cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, const Mat34 &M_d, float4 *vtx,
+                           float4 *nrm, cudaStream_t st);
+cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 &M_d, uint32_t *rmin, uint32_t *rmax,
+                                 cudaStream_t st);
+bool range_fits(const Intr &in);
 cudaError_t launch_depth_u16(const uint16_t *raw, float *out, int64_t n, cudaStream_t st);
 cudaError_t launch_reset(const SceneDev &s, cudaStream_t st);
 }  // namespace itm

@@ -19,11 +19,24 @@
 // the trilinear field at +-1 voxel per axis, emitted only when all 48 voxels
 // read are allocated and observed (weight > 0).
 //
+// Search range (Sec. 4.4, second half): before the march, every allocated
+// block is projected into the image and each 8x4-pixel tile (the pixels of
+// one warp) records the nearest and farthest camera depth of the blocks that
+// cover it.  A block's extent here is its query region -- the points whose
+// nearest voxel lies in it, [8b - 1/2, 8b + 15/2] voxels per axis -- clipped
+// to z >= z_min, grown by a small margin.  The march uses the range without
+// changing its result: coarse steps in front of the tile's nearest depth are
+// replayed as additions (no hash probes, the same t sequence and iteration
+// count), and a ray in COARSE or FINE beyond the tile's farthest depth can
+// only miss.  The paper renders 16x16-pixel fragments with per-pixel atomic
+// min/max; here the fragment is the warp's tile and the atomics go to one
+// word per tile.
+//
 // The per-iteration "is the block at p allocated" query runs with the whole
 // warp converged: lanes asking for the same block are grouped with
 // __match_any_sync and one lane per group walks the hash chain (Sec. 3.3),
-// the others take its answer by shuffle.  Every arithmetic step uses IEEE
-// round-to-nearest operations in a fixed order.
+// the others take its answer by shuffle.  Every arithmetic step of the march
+// uses IEEE round-to-nearest operations in a fixed order.
 #include "itm_internal.cuh"
 
 namespace itm {
@@ -32,13 +45,15 @@ namespace {
 
 enum { COARSE = 0, FINE = 1, SURFACE = 2, BEHIND = 3, WRONG = 4, MISS = 5 };
 
+constexpr float kRangeMarginZ = 1e-4f;  // metres, covers rounding of p(t) vs t
+constexpr float kRangeMarginPx = 1.0f;  // pixels
+
 __device__ __forceinline__ bool coord_ok(float q) { return q > -262000.0f && q < 262000.0f; }
 __device__ __forceinline__ bool in_i16(int v) { return v >= -32768 && v <= 32767; }
 
 __device__ __forceinline__ float lerp_rn(float a, float b, float t) { return fadd(a, fmul(t, fsub(b, a))); }
 
-// Block index of block (bx, by, bz) or -1; a per-thread one-entry cache
-// holds the last answer.
+// One-entry cache of the last block looked up by this thread.
 struct BlockCache {
     unsigned long long key;
     int ptr;
@@ -54,37 +69,46 @@ __device__ __forceinline__ int cached_lookup(const SceneDev &s, BlockCache &c, i
     return c.ptr;
 }
 
-// Voxel value and "observed" flag (allocated with weight > 0).
-template <int MODE>
-__device__ __forceinline__ float voxel_at(const SceneDev &s, int ptr, int gx, int gy, int gz, bool &obs)
+template <int MODE, bool OBS>
+__device__ __forceinline__ float voxel_at(const SceneDev &s, int ptr, int gx, int gy, int gz, bool &all_obs)
 {
     if (ptr < 0) {
-        obs = false;
+        if (OBS) all_obs = false;
         return 1.0f;
     }
     const size_t i = (size_t)ptr * kBlockVoxels + (gx & 7) + 8 * (gy & 7) + 64 * (gz & 7);
-    if (MODE == 0) obs = __ldg(&s.w8[i]) != 0;
-    else obs = __ldg(&s.w32[i]) > 0.0f;
+    if (OBS) {
+        if (MODE == 0) all_obs = all_obs && (__ldg(&s.w8[i]) != 0);
+        else all_obs = all_obs && (__ldg(&s.w32[i]) > 0.0f);
+    }
     return __ldg(&s.sdf[i]);
 }
 
-// Trilinear interpolation at voxel coordinates q; clears all_obs when one of
-// the eight voxels is unallocated or unobserved.
-template <int MODE>
-__device__ float trilinear(const SceneDev &s, BlockCache &c, const float q[3], bool &all_obs)
+// Trilinear interpolation at voxel coordinates (q0, q1, q2).  Each distinct
+// block under the 2x2x2 stencil is looked up once.  With OBS, all_obs is
+// cleared when one of the eight voxels is unallocated or unobserved.
+template <int MODE, bool OBS>
+__device__ __forceinline__ float trilinear(const SceneDev &s, BlockCache &c, float q0, float q1, float q2,
+                                           bool &all_obs)
 {
-    const float g0x = floorf(q[0]), g0y = floorf(q[1]), g0z = floorf(q[2]);
-    const float fx = fsub(q[0], g0x), fy = fsub(q[1], g0y), fz = fsub(q[2], g0z);
+    const float g0x = floorf(q0), g0y = floorf(q1), g0z = floorf(q2);
+    const float fx = fsub(q0, g0x), fy = fsub(q1, g0y), fz = fsub(q2, g0z);
     const int x = (int)g0x, y = (int)g0y, z = (int)g0z;
+    const int bx = x >> 3, by = y >> 3, bz = z >> 3;
+    const bool cx = (x & 7) == 7, cy = (y & 7) == 7, cz = (z & 7) == 7;
+    int P[8];
+    P[0] = cached_lookup(s, c, bx, by, bz);
+    P[1] = cx ? cached_lookup(s, c, bx + 1, by, bz) : P[0];
+    P[2] = cy ? cached_lookup(s, c, bx, by + 1, bz) : P[0];
+    P[3] = cy ? (cx ? cached_lookup(s, c, bx + 1, by + 1, bz) : P[2]) : P[1];
+    P[4] = cz ? cached_lookup(s, c, bx, by, bz + 1) : P[0];
+    P[5] = cz ? (cx ? cached_lookup(s, c, bx + 1, by, bz + 1) : P[4]) : P[1];
+    P[6] = cz ? (cy ? cached_lookup(s, c, bx, by + 1, bz + 1) : P[4]) : P[2];
+    P[7] = cz ? (cy ? (cx ? cached_lookup(s, c, bx + 1, by + 1, bz + 1) : P[6]) : P[5]) : P[3];
     float cv[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {
-        const int gx = x + (k & 1), gy = y + ((k >> 1) & 1), gz = z + ((k >> 2) & 1);
-        const int ptr = cached_lookup(s, c, gx >> 3, gy >> 3, gz >> 3);
-        bool o;
-        cv[k] = voxel_at<MODE>(s, ptr, gx, gy, gz, o);
-        all_obs = all_obs && o;
-    }
+    for (int k = 0; k < 8; ++k)
+        cv[k] = voxel_at<MODE, OBS>(s, P[k], x + (k & 1), y + ((k >> 1) & 1), z + ((k >> 2) & 1), all_obs);
     const float c00 = lerp_rn(cv[0], cv[1], fx);
     const float c10 = lerp_rn(cv[2], cv[3], fx);
     const float c01 = lerp_rn(cv[4], cv[5], fx);
@@ -94,10 +118,115 @@ __device__ float trilinear(const SceneDev &s, BlockCache &c, const float q[3], b
     return lerp_rn(c0, c1, fz);
 }
 
-template <int MODE>
+// ------------------------------------------------------------ search range
+
+struct TileRange {
+    int tx0, tx1, ty0, ty1;
+    float zlo, zhi;
+};
+
+// Conservative tile rectangle and depth range of block b's query region
+// clipped to z >= zc.  Returns false when the region cannot be met by a ray.
+__device__ bool block_tile_range(short4 b, const Mat34 &M, const Intr &in, float vs, float zc, int tiles_x,
+                                 int tiles_y, TileRange &r)
+{
+    const float eps = 1e-5f;
+    const float lo[3] = {((float)(b.x * 8) - 0.51f) * vs - eps, ((float)(b.y * 8) - 0.51f) * vs - eps,
+                         ((float)(b.z * 8) - 0.51f) * vs - eps};
+    const float hi[3] = {((float)(b.x * 8) + 7.51f) * vs + eps, ((float)(b.y * 8) + 7.51f) * vs + eps,
+                         ((float)(b.z * 8) + 7.51f) * vs + eps};
+    float X[8], Y[8], Z[8];
+    float zmax = -3.0e38f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float px = (c & 1) ? hi[0] : lo[0], py = (c & 2) ? hi[1] : lo[1], pz = (c & 4) ? hi[2] : lo[2];
+        X[c] = M.m[0] * px + M.m[1] * py + M.m[2] * pz + M.m[3];
+        Y[c] = M.m[4] * px + M.m[5] * py + M.m[6] * pz + M.m[7];
+        Z[c] = M.m[8] * px + M.m[9] * py + M.m[10] * pz + M.m[11];
+        zmax = fmaxf(zmax, Z[c]);
+    }
+    if (zmax < zc) return false;
+    float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f, zmin = 3.0e38f;
+    auto add_point = [&](float x, float y, float z) {
+        const float u = in.fx * x / z + in.cx, v = in.fy * y / z + in.cy;
+        umin = fminf(umin, u);
+        umax = fmaxf(umax, u);
+        vmin = fminf(vmin, v);
+        vmax = fmaxf(vmax, v);
+        zmin = fminf(zmin, z);
+    };
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        if (Z[c] >= zc) add_point(X[c], Y[c], Z[c]);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int d = c | (1 << a);
+            if (d == c) continue;
+            // edge c-d crosses the plane z = zc
+            if ((Z[c] < zc) != (Z[d] < zc)) {
+                const float w = (zc - Z[c]) / (Z[d] - Z[c]);
+                add_point(X[c] + w * (X[d] - X[c]), Y[c] + w * (Y[d] - Y[c]), zc);
+            }
+        }
+    }
+    if (!(umax >= -kRangeMarginPx && vmax >= -kRangeMarginPx && umin <= (float)in.W - 1.0f + kRangeMarginPx &&
+          vmin <= (float)in.H - 1.0f + kRangeMarginPx))
+        return false;
+    const float u0 = fmaxf(umin - kRangeMarginPx, 0.0f), u1 = fminf(umax + kRangeMarginPx, (float)(in.W - 1));
+    const float v0 = fmaxf(vmin - kRangeMarginPx, 0.0f), v1 = fminf(vmax + kRangeMarginPx, (float)(in.H - 1));
+    r.tx0 = min((int)u0 >> 3, tiles_x - 1);
+    r.tx1 = min((int)u1 >> 3, tiles_x - 1);
+    r.ty0 = min((int)v0 >> 2, tiles_y - 1);
+    r.ty1 = min((int)v1 >> 2, tiles_y - 1);
+    r.zlo = fmaxf(zmin - kRangeMarginZ, 0.0f);
+    r.zhi = zmax + kRangeMarginZ;
+    return r.tx0 <= r.tx1 && r.ty0 <= r.ty1;
+}
+
+// One warp takes 32 allocated blocks; their tile rectangles are then
+// rasterised by the whole warp, block after block, with atomic min/max on the
+// float bits (non-negative floats order like their bit patterns).
+__global__ void __launch_bounds__(256) range_kernel(SceneDev s, Mat34 M, Intr in, float zc, int tiles_x,
+                                                    int tiles_y, uint32_t *__restrict__ rmin,
+                                                    uint32_t *__restrict__ rmax)
+{
+    const int n = min(__ldcg(&s.ctr->block_head), s.nv);
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n; base += warps * 32) {
+        const int i = base + lane;
+        TileRange r{0, -1, 0, -1, 0.f, 0.f};
+        bool ok = false;
+        if (i < n) {
+            const int ptr = __ldg(&s.block_free[i]);
+            const short4 b = __ldg(&s.block_pos[ptr]);
+            if (b.w) ok = block_tile_range(b, M, in, s.voxel_size, zc, tiles_x, tiles_y, r);
+        }
+        unsigned todo = __ballot_sync(kFull, ok);
+        while (todo) {
+            const int j = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const int tx0 = __shfl_sync(kFull, r.tx0, j), tx1 = __shfl_sync(kFull, r.tx1, j);
+            const int ty0 = __shfl_sync(kFull, r.ty0, j), ty1 = __shfl_sync(kFull, r.ty1, j);
+            const uint32_t zlo = __float_as_uint(__shfl_sync(kFull, r.zlo, j));
+            const uint32_t zhi = __float_as_uint(__shfl_sync(kFull, r.zhi, j));
+            const int w = tx1 - tx0 + 1, cnt = w * (ty1 - ty0 + 1);
+            for (int k = lane; k < cnt; k += 32) {
+                const int t = (ty0 + k / w) * tiles_x + tx0 + k % w;
+                atomicMin(&rmin[t], zlo);
+                atomicMax(&rmax[t], zhi);
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- march
+
+template <int MODE, bool RANGE>
 __global__ void __launch_bounds__(256) raycast_kernel(SceneDev s, Intr in, Mat34 T, float4 *__restrict__ vtx,
                                                       float4 *__restrict__ nrm, int max_iter, float tB_m,
-                                                      float inv_sv)
+                                                      float inv_sv, const uint32_t *__restrict__ rmin,
+                                                      const uint32_t *__restrict__ rmax, int tiles_x, int tiles_y)
 {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int u = blockIdx.x * 32 + (warp & 3) * 8 + (lane & 7);
@@ -120,12 +249,40 @@ __global__ void __launch_bounds__(256) raycast_kernel(SceneDev s, Intr in, Mat34
     float t = s.z_min;
     int state = inside ? COARSE : MISS;
     int it = 0;
-    float q[3];
+    float tlo = 0.0f, thi = 3.0e38f;
+    const int tix = blockIdx.x * 4 + (warp & 3), tiy = blockIdx.y * 2 + (warp >> 2);
+    if (RANGE && tix < tiles_x && tiy < tiles_y) {
+        // the warp's pixels form one tile (a tile outside the image has no pixel inside)
+        const int tile = tiy * tiles_x + tix;
+        const uint32_t lo = __ldg(&rmin[tile]), hi = __ldg(&rmax[tile]);
+        if (lo == 0xffffffffu) {
+            tlo = thi = -1.0f;  // no block covers the tile
+        } else {
+            tlo = __uint_as_float(lo);
+            thi = __uint_as_float(hi);
+        }
+        if (state == COARSE) {
+            if (thi < 0.0f) {
+                state = MISS;
+            } else {
+                // the oracle's coarse steps in front of every block: t += tB each
+                while (t < tlo && it < max_iter && t <= s.z_max) {
+                    t = fadd(t, tB);
+                    ++it;
+                }
+            }
+        }
+    }
+    float q[3] = {0.f, 0.f, 0.f};
 
     while (__any_sync(kFull, state <= SURFACE)) {
         bool marching = state <= SURFACE;
         if (marching && !(it < max_iter && t <= s.z_max)) {
             state = MISS;
+            marching = false;
+        }
+        if (RANGE && marching && state != SURFACE && t > thi) {
+            state = MISS;  // only unallocated space ahead: the march can only miss
             marching = false;
         }
         bool ok = marching;
@@ -171,8 +328,8 @@ __global__ void __launch_bounds__(256) raycast_kernel(SceneDev s, Intr in, Mat34
             else state = COARSE;
             continue;
         }
-        bool obs = true;
-        const float F = trilinear<MODE>(s, cache, q, obs);
+        bool unused = true;
+        const float F = trilinear<MODE, false>(s, cache, q[0], q[1], q[2], unused);
         if (state == FINE) {
             if (F <= 0.0f) {
                 state = WRONG;
@@ -195,8 +352,8 @@ __global__ void __launch_bounds__(256) raycast_kernel(SceneDev s, Intr in, Mat34
         for (int r = 0; r < 2; ++r) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) q[i] = fmul(fadd(org[i], fmul(t, dir[i])), inv_sv);
-            bool obs = true;
-            const float F = trilinear<MODE>(s, cache, q, obs);
+            bool unused = true;
+            const float F = trilinear<MODE, false>(s, cache, q[0], q[1], q[2], unused);
             t = fadd(t, fmul(F, tmu));
         }
         float p[3];
@@ -207,29 +364,51 @@ __global__ void __launch_bounds__(256) raycast_kernel(SceneDev s, Intr in, Mat34
         }
         if (coord_ok(q[0]) && coord_ok(q[1]) && coord_ok(q[2])) {
             V = make_float4(p[0], p[1], p[2], 1.0f);
-            float g[3];
             bool obs = true;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                float qp[3] = {q[0], q[1], q[2]}, qm[3] = {q[0], q[1], q[2]};
-                qp[a] = fadd(q[a], 1.0f);
-                qm[a] = fsub(q[a], 1.0f);
-                const float fp = trilinear<MODE>(s, cache, qp, obs);
-                const float fm = trilinear<MODE>(s, cache, qm, obs);
-                g[a] = fsub(fp, fm);
-            }
-            const float gl = __fsqrt_rn(fadd(fadd(fmul(g[0], g[0]), fmul(g[1], g[1])), fmul(g[2], g[2])));
-            if (obs && gl > 0.0f) N = make_float4(fdiv(g[0], gl), fdiv(g[1], gl), fdiv(g[2], gl), 1.0f);
+            const float gx = fsub(trilinear<MODE, true>(s, cache, fadd(q[0], 1.0f), q[1], q[2], obs),
+                                  trilinear<MODE, true>(s, cache, fsub(q[0], 1.0f), q[1], q[2], obs));
+            const float gy = fsub(trilinear<MODE, true>(s, cache, q[0], fadd(q[1], 1.0f), q[2], obs),
+                                  trilinear<MODE, true>(s, cache, q[0], fsub(q[1], 1.0f), q[2], obs));
+            const float gz = fsub(trilinear<MODE, true>(s, cache, q[0], q[1], fadd(q[2], 1.0f), obs),
+                                  trilinear<MODE, true>(s, cache, q[0], q[1], fsub(q[2], 1.0f), obs));
+            const float gl = __fsqrt_rn(fadd(fadd(fmul(gx, gx), fmul(gy, gy)), fmul(gz, gz)));
+            if (obs && gl > 0.0f) N = make_float4(fdiv(gx, gl), fdiv(gy, gl), fdiv(gz, gl), 1.0f);
         }
     }
     vtx[o] = V;
     nrm[o] = N;
 }
 
+int range_grid()
+{
+    static int g = 0;
+    if (!g) {
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        g = sms * 4;
+    }
+    return g;
+}
+
 }  // namespace
 
-cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, float4 *vtx, float4 *nrm,
-                           cudaStream_t st)
+bool range_fits(const Intr &in) { return in.W <= kRangeMaxW && in.H <= kRangeMaxH; }
+
+cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 &M_d, uint32_t *rmin, uint32_t *rmax,
+                                 cudaStream_t st)
+{
+    const int tx = (in.W + 7) / 8, ty = (in.H + 3) / 4;
+    cudaError_t e = cudaMemsetAsync(rmin, 0xff, sizeof(uint32_t) * (size_t)tx * ty, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(rmax, 0, sizeof(uint32_t) * (size_t)tx * ty, st);
+    if (e != cudaSuccess) return e;
+    const float zc = s.z_min - 1e-3f;
+    range_kernel<<<range_grid(), 256, 0, st>>>(s, M_d, in, zc, tx, ty, rmin, rmax);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, const Mat34 &M_d, float4 *vtx,
+                           float4 *nrm, cudaStream_t st)
 {
     // host-side constants with the same float operations as the oracle
     volatile float span = s.z_max - s.z_min;
@@ -239,10 +418,24 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
     volatile float tB_m = 8.0f * s.voxel_size;
     const float inv_sv = (float)(1.0 / (double)s.voxel_size);  // voxel coordinates: p * (1/s), 1/s rounded once
     dim3 grid((in.W + 31) / 32, (in.H + 7) / 8);
-    if (s.weight_mode == 0)
-        raycast_kernel<0><<<grid, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv);
-    else
-        raycast_kernel<1><<<grid, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv);
+    const int tx = (in.W + 7) / 8, ty = (in.H + 3) / 4;
+    if (range_fits(in)) {
+        cudaError_t e = launch_raycast_range(s, in, M_d, s.range_min, s.range_max, st);
+        if (e != cudaSuccess) return e;
+        if (s.weight_mode == 0)
+            raycast_kernel<0, true><<<grid, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
+                                                          s.range_max, tx, ty);
+        else
+            raycast_kernel<1, true><<<grid, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
+                                                          s.range_max, tx, ty);
+    } else {
+        if (s.weight_mode == 0)
+            raycast_kernel<0, false><<<grid, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, nullptr,
+                                                           nullptr, tx, ty);
+        else
+            raycast_kernel<1, false><<<grid, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, nullptr,
+                                                           nullptr, tx, ty);
+    }
     return cudaGetLastError();
 }
 

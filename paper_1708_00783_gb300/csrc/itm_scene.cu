@@ -82,7 +82,7 @@ static int valid_params(const itm_scene_params *p)
 static void free_dev(SceneDev &d)
 {
     void *ptrs[] = {d.entries, d.req, d.req_list, d.overflow, d.visible, d.block_pos, d.sdf,
-                    d.w8, d.w32, d.block_free, d.excess_free, d.ctr};
+                    d.w8, d.w32, d.block_free, d.excess_free, d.ctr, d.range_min, d.range_max};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     memset(&d, 0, sizeof(d));
@@ -141,6 +141,8 @@ int itm_scene_create(const itm_scene_params *params, itm_scene **out)
     ITM_ALLOC(d.block_free, sizeof(int32_t) * (size_t)(d.nv > 0 ? d.nv : 1));
     ITM_ALLOC(d.excess_free, sizeof(int32_t) * (size_t)(d.ne > 0 ? d.ne : 1));
     ITM_ALLOC(d.ctr, sizeof(Counters));
+    ITM_ALLOC(d.range_min, sizeof(uint32_t) * (size_t)kRangeMaxTiles);
+    ITM_ALLOC(d.range_max, sizeof(uint32_t) * (size_t)kRangeMaxTiles);
 #undef ITM_ALLOC
     if (e == cudaSuccess) e = launch_reset(d, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
@@ -214,12 +216,25 @@ int itm_raycast(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16],
     if (!sc || !valid_pose(T_wc) || !vertex_dev || !normal_dev || !valid_intr(intr)) return ITM_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(vertex_dev) & 15) || (reinterpret_cast<uintptr_t>(normal_dev) & 15))
         return ITM_ERR_ARG;
-    Mat34 T;
+    Mat34 T, M;
     pose_rows(T_wc, T);
+    rigid_inverse_rows(T_wc, M);
     cudaStream_t st = (cudaStream_t)stream;
     sc->last_stream = st;
-    return check_cuda(launch_raycast(sc->d, to_intr(intr), T, reinterpret_cast<float4 *>(vertex_dev),
+    return check_cuda(launch_raycast(sc->d, to_intr(intr), T, M, reinterpret_cast<float4 *>(vertex_dev),
                                      reinterpret_cast<float4 *>(normal_dev), st));
+}
+
+int itm_raycast_range(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16], float *zmin_dev,
+                      float *zmax_dev, itm_stream stream)
+{
+    if (!sc || !valid_pose(T_wc) || !zmin_dev || !zmax_dev || !valid_intr(intr)) return ITM_ERR_ARG;
+    Mat34 M;
+    rigid_inverse_rows(T_wc, M);
+    cudaStream_t st = (cudaStream_t)stream;
+    sc->last_stream = st;
+    return check_cuda(launch_raycast_range(sc->d, to_intr(intr), M, reinterpret_cast<uint32_t *>(zmin_dev),
+                                           reinterpret_cast<uint32_t *>(zmax_dev), st));
 }
 
 int itm_process_frame(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],

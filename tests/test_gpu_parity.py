@@ -271,3 +271,54 @@ def test_large_scale_frames(itm):
         compare_volumes(g.export(), o.export())
         if nb == 1 << 18:
             assert g.stats()["excess_used"] > 0
+
+
+def _novel_pose(T, yaw_deg, back):
+    """The pose turned about its own y axis and moved back along its view axis."""
+    a = np.radians(yaw_deg)
+    Ry = np.array([[np.cos(a), 0, np.sin(a)], [0, 1, 0], [-np.sin(a), 0, np.cos(a)]])
+    N = np.asarray(T, dtype=np.float64).copy()
+    N[:3, :3] = N[:3, :3] @ Ry
+    N[:3, 3] = N[:3, 3] - back * N[:3, 2]
+    return N.astype(np.float32)
+
+
+def test_raycast_range_bounds_hits_and_novel_views(itm):
+    """Sec. 4.4 search range: each tile's [zmin, zmax] covers the depth of
+    every hit in it (within mu: the two refinement steps may move the hit
+    out of the block region that stopped the march), tiles with no block
+    have no hit; raycasts from views that were never fused match the oracle."""
+    import torch
+    w = tiny_workload()
+    g, o, _ = run_pair(itm, w, range(w.n_frames))
+    ci = intr_of(itm, w.intr)
+    H, W = w.intr.height, w.intr.width
+    tx, ty = (W + 7) // 8, (H + 3) // 4
+    mu = w.params["mu"]
+    vtx = torch.zeros((H, W, 4), dtype=torch.float32, device="cuda")
+    nrm = torch.zeros_like(vtx)
+    zmin = torch.zeros(ty * tx, dtype=torch.float32, device="cuda")
+    zmax = torch.zeros_like(zmin)
+    base = w.frame(4).T_wc
+    for yaw, back in ((0.0, 0.0), (12.0, 0.3), (-20.0, -0.5), (35.0, 0.8)):
+        T = _novel_pose(base, yaw, back)
+        itm.itm_raycast_range(g.handle, ci, T, zmin, zmax)
+        g.raycast(ci, T, vtx, nrm)
+        torch.cuda.synchronize()
+        vo, no = o.raycast(W, H, w.intr.as_array(), T)
+        rep = compare_raycast(vtx.cpu().numpy(), nrm.cpu().numpy(), vo, no, T)
+        assert rep["bitexact_frac"] >= 0.999, rep
+        lo = zmin.cpu().numpy().reshape(ty, tx)
+        hi = zmax.cpu().numpy().reshape(ty, tx)
+        hit = vo[..., 3] > 0
+        vv, uu = np.nonzero(hit)
+        z = camera_depth_of(vo, T)[hit]
+        tlo, thi = lo[vv // 4, uu // 8], hi[vv // 4, uu // 8]
+        assert np.all(np.isfinite(tlo)), "a hit in a tile no block covers"
+        assert np.all(z >= tlo - mu) and np.all(z <= thi + mu)
+        assert np.isnan(lo).any() or rep["hits"] > 0
+
+
+def camera_depth_of(vtx, T):
+    from tests.parity_util import camera_depth
+    return camera_depth(vtx, T)
