@@ -76,6 +76,17 @@ def _load():
     lib.orc_export.argtypes = [P, i16p, P, P, ctypes.c_int]
     lib.orc_entries.argtypes = [P, i32p]
     lib.orc_depth_u16_to_f32.argtypes = [u16p, f32p, ctypes.c_longlong]
+    f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+    lib.orc_bf16.restype = ctypes.c_float
+    lib.orc_bf16.argtypes = [ctypes.c_float]
+    lib.orc_conf_features.restype = ctypes.c_int
+    lib.orc_conf_features.argtypes = [f32p, ctypes.c_int, ctypes.c_int, f32p, ctypes.c_float, ctypes.c_int,
+                                      ctypes.c_int, f64p]
+    lib.orc_mlp_forward.restype = ctypes.c_double
+    lib.orc_mlp_forward.argtypes = [f32p, f64p, ctypes.c_int, P, P]
+    lib.orc_mlp_loss_grad.restype = ctypes.c_double
+    lib.orc_mlp_loss_grad.argtypes = [f32p, f64p, f32p, ctypes.c_int, ctypes.c_int, f64p]
+    lib.orc_conf_weights.argtypes = [f32p, ctypes.c_int, ctypes.c_int, f32p, ctypes.c_float, f32p, f32p]
     _lib = lib
     return lib
 
@@ -169,3 +180,50 @@ class Scene:
         out = np.zeros((nb + ne, 5), dtype=np.int32)
         _load().orc_entries(self.p, out)
         return out
+
+
+# ------------------------------------------------------- learned confidence
+
+N_FEATURES = 52
+N_HIDDEN = 64
+N_PARAMS = N_HIDDEN * N_FEATURES + N_HIDDEN + N_HIDDEN * N_HIDDEN + N_HIDDEN + N_HIDDEN + 1
+
+
+def bf16(x) -> np.ndarray:
+    lib = _load()
+    a = np.asarray(x, dtype=np.float32)
+    return np.vectorize(lambda v: lib.orc_bf16(float(v)), otypes=[np.float32])(a)
+
+
+def conf_features(depth, intr, mu, u, v):
+    """52 features of pixel (u, v) (fp64) and whether the pixel has depth."""
+    d = _f32(depth)
+    H, W = d.shape
+    x = np.zeros(N_FEATURES, dtype=np.float64)
+    ok = _load().orc_conf_features(d, W, H, _f32(intr), mu, int(u), int(v), x)
+    return x, bool(ok)
+
+
+def mlp_forward(params, x, round_bf16=True):
+    """(logit, h1, h2) of one feature vector."""
+    h1 = np.zeros(N_HIDDEN, dtype=np.float64)
+    h2 = np.zeros(N_HIDDEN, dtype=np.float64)
+    o = _load().orc_mlp_forward(_f32(params), np.ascontiguousarray(x, dtype=np.float64), int(round_bf16),
+                                h1.ctypes.data, h2.ctypes.data)
+    return o, h1, h2
+
+
+def mlp_loss_grad(params, X, y, round_bf16=True):
+    """Mean BCE loss and its gradient (fp64, length N_PARAMS)."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    g = np.zeros(N_PARAMS, dtype=np.float64)
+    loss = _load().orc_mlp_loss_grad(_f32(params), X, _f32(y), X.shape[0], int(round_bf16), g)
+    return loss, g
+
+
+def conf_weights(depth, intr, mu, params):
+    d = _f32(depth)
+    H, W = d.shape
+    out = np.zeros((H, W), dtype=np.float32)
+    _load().orc_conf_weights(d, W, H, _f32(intr), mu, _f32(params), out)
+    return out

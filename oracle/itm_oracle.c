@@ -599,3 +599,177 @@ void orc_depth_u16_to_f32(const uint16_t *raw, float *out, long long n)
 {
     for (long long i = 0; i < n; ++i) out[i] = (float)raw[i] / 1000.0f;
 }
+
+/* ------------------------------------------------ learned confidence weight
+ *
+ * Not in the paper: a per-pixel observation weight w_px in [0, 1] replaces the
+ * constant 1 of the Sec. 4.3 listing.  Readings (all silent in the paper):
+ *   features (52): the 7x7 depth patch around the pixel, entry (i, j) for row
+ *     offset i and column offset j in -3..3 at index (i+3)*7 + (j+3), equal to
+ *     clamp((D(u+j, v+i) - D(u, v)) / mu, -4, 4) when that pixel is inside the
+ *     image with depth > 0, else 0; then the unit normal of the back-projected
+ *     depth, P(u, v) = D(u, v) ((u-cx)/fx, (v-cy)/fy, 1),
+ *     n = normalise((P(u,v+1) - P(u,v-1)) x (P(u+1,v) - P(u-1,v))) (facing the
+ *     camera), or 0 when a neighbour is outside or has no depth.
+ *   network: h1 = relu(W1 x + b1) (64), h2 = relu(W2 h1 + b2) (64),
+ *     o = w3 . h2 + b3, w_px = 1 / (1 + exp(-o)).
+ *   parameters (fp32, 7617): W1[64][52], b1[64], W2[64][64], b2[64], w3[64], b3.
+ *   with round_bf16, W1, W2 and the inputs of both matrix products (x, h1)
+ *     are rounded to bfloat16 (round to nearest even), as the tensor cores
+ *     consume them; everything else is fp64 here.
+ *   loss: mean binary cross-entropy of w_px against labels y in {0, 1}.
+ */
+
+#define ORC_NF 52
+#define ORC_NH 64
+#define ORC_NP (ORC_NH * ORC_NF + ORC_NH + ORC_NH * ORC_NH + ORC_NH + ORC_NH + 1)
+
+/* bfloat16 round to nearest even of a finite float, returned as float */
+float orc_bf16(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    u &= 0xffff0000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+static double depth_at(const float *D, int W, int H, int u, int v)
+{
+    if (u < 0 || v < 0 || u >= W || v >= H) return 0.0;
+    float d = D[(size_t)v * W + u];
+    return d > 0.0f ? (double)d : 0.0;
+}
+
+/* Features of pixel (u, v); returns 0 (features all zero) when the pixel has
+ * no depth. */
+int orc_conf_features(const float *D, int W, int H, const float intr[4], float mu, int u, int v, double *x)
+{
+    for (int k = 0; k < ORC_NF; ++k) x[k] = 0.0;
+    double dc = depth_at(D, W, H, u, v);
+    if (dc <= 0.0) return 0;
+    for (int i = -3; i <= 3; ++i)
+        for (int j = -3; j <= 3; ++j) {
+            double d = depth_at(D, W, H, u + j, v + i);
+            double f = 0.0;
+            if (d > 0.0) {
+                f = (d - dc) / (double)mu;
+                if (f > 4.0) f = 4.0;
+                if (f < -4.0) f = -4.0;
+            }
+            x[(i + 3) * 7 + (j + 3)] = f;
+        }
+    double dl = depth_at(D, W, H, u - 1, v), dr = depth_at(D, W, H, u + 1, v);
+    double du = depth_at(D, W, H, u, v - 1), dd = depth_at(D, W, H, u, v + 1);
+    if (dl > 0.0 && dr > 0.0 && du > 0.0 && dd > 0.0) {
+        const double fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3];
+        double Pl[3] = {dl * ((u - 1) - cx) / fx, dl * (v - cy) / fy, dl};
+        double Pr[3] = {dr * ((u + 1) - cx) / fx, dr * (v - cy) / fy, dr};
+        double Pu[3] = {du * (u - cx) / fx, du * ((v - 1) - cy) / fy, du};
+        double Pd[3] = {dd * (u - cx) / fx, dd * ((v + 1) - cy) / fy, dd};
+        double a[3] = {Pd[0] - Pu[0], Pd[1] - Pu[1], Pd[2] - Pu[2]};  /* along +v */
+        double b[3] = {Pr[0] - Pl[0], Pr[1] - Pl[1], Pr[2] - Pl[2]};  /* along +u */
+        double n[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};
+        double l = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (l > 0.0) {
+            x[49] = n[0] / l;
+            x[50] = n[1] / l;
+            x[51] = n[2] / l;
+        }
+    }
+    return 1;
+}
+
+static double relu(double a) { return a > 0.0 ? a : 0.0; }
+
+static double maybe_bf16(double v, int r) { return r ? (double)orc_bf16((float)v) : v; }
+
+/* Forward pass; returns the logit o.  h1, h2 (nullable) receive the hidden
+ * activations, xr (nullable) the inputs as consumed. */
+double orc_mlp_forward(const float *P, const double *x, int round_bf16, double *h1, double *h2)
+{
+    const float *W1 = P, *b1 = W1 + ORC_NH * ORC_NF, *W2 = b1 + ORC_NH, *b2 = W2 + ORC_NH * ORC_NH;
+    const float *w3 = b2 + ORC_NH, *b3 = w3 + ORC_NH;
+    double xin[ORC_NF], a1[ORC_NH], a1in[ORC_NH], a2[ORC_NH];
+    for (int k = 0; k < ORC_NF; ++k) xin[k] = maybe_bf16(x[k], round_bf16);
+    for (int m = 0; m < ORC_NH; ++m) {
+        double acc = 0.0;
+        for (int k = 0; k < ORC_NF; ++k) acc += maybe_bf16(W1[m * ORC_NF + k], round_bf16) * xin[k];
+        a1[m] = relu(acc + b1[m]);
+        a1in[m] = maybe_bf16(a1[m], round_bf16);
+    }
+    double o = b3[0];
+    for (int n = 0; n < ORC_NH; ++n) {
+        double acc = 0.0;
+        for (int m = 0; m < ORC_NH; ++m) acc += maybe_bf16(W2[n * ORC_NH + m], round_bf16) * a1in[m];
+        a2[n] = relu(acc + b2[n]);
+        o += (double)w3[n] * a2[n];
+    }
+    if (h1)
+        for (int m = 0; m < ORC_NH; ++m) h1[m] = a1[m];
+    if (h2)
+        for (int n = 0; n < ORC_NH; ++n) h2[n] = a2[n];
+    return o;
+}
+
+/* Mean binary cross-entropy over n samples (X: n x 52, y: n) and its
+ * gradient with respect to the 7617 parameters (grad, fp64).  With
+ * round_bf16 the forward uses the rounded weights and inputs and the
+ * gradient treats the rounding as the identity. */
+double orc_mlp_loss_grad(const float *P, const double *X, const float *y, int n, int round_bf16, double *grad)
+{
+    const float *W1 = P, *b1 = W1 + ORC_NH * ORC_NF, *W2 = b1 + ORC_NH, *b2 = W2 + ORC_NH * ORC_NH;
+    const float *w3 = b2 + ORC_NH;
+    double *gW1 = grad, *gb1 = gW1 + ORC_NH * ORC_NF, *gW2 = gb1 + ORC_NH, *gb2 = gW2 + ORC_NH * ORC_NH;
+    double *gw3 = gb2 + ORC_NH, *gb3 = gw3 + ORC_NH;
+    for (int i = 0; i < ORC_NP; ++i) grad[i] = 0.0;
+    double loss = 0.0;
+    double h1[ORC_NH], h2[ORC_NH], d2[ORC_NH], d1[ORC_NH];
+    for (int s = 0; s < n; ++s) {
+        const double *x = X + (size_t)s * ORC_NF;
+        double o = orc_mlp_forward(P, x, round_bf16, h1, h2);
+        double p = 1.0 / (1.0 + exp(-o));
+        double t = y[s];
+        /* log(1 + exp(-|o|)) form of the cross-entropy */
+        loss += (o > 0 ? o : 0.0) - o * t + log1p(exp(-fabs(o)));
+        double dout = (p - t) / n;
+        gb3[0] += dout;
+        for (int k = 0; k < ORC_NH; ++k) {
+            gw3[k] += dout * h2[k];
+            d2[k] = h2[k] > 0.0 ? dout * w3[k] : 0.0;
+            gb2[k] += d2[k];
+        }
+        for (int a = 0; a < ORC_NH; ++a)
+            for (int m = 0; m < ORC_NH; ++m) gW2[a * ORC_NH + m] += d2[a] * maybe_bf16(h1[m], round_bf16);
+        for (int m = 0; m < ORC_NH; ++m) {
+            double acc = 0.0;
+            for (int a = 0; a < ORC_NH; ++a) acc += maybe_bf16(W2[a * ORC_NH + m], round_bf16) * d2[a];
+            d1[m] = h1[m] > 0.0 ? acc : 0.0;
+            gb1[m] += d1[m];
+        }
+        for (int m = 0; m < ORC_NH; ++m)
+            for (int k = 0; k < ORC_NF; ++k) gW1[m * ORC_NF + k] += d1[m] * maybe_bf16(x[k], round_bf16);
+    }
+    (void)W1;
+    (void)b1;
+    (void)b2;
+    return loss / n;
+}
+
+/* w_px for every pixel of a frame (0 where the pixel has no depth). */
+void orc_conf_weights(const float *D, int W, int H, const float intr[4], float mu, const float *P, float *wpx)
+{
+    double x[ORC_NF];
+    for (int v = 0; v < H; ++v)
+        for (int u = 0; u < W; ++u) {
+            if (!orc_conf_features(D, W, H, intr, mu, u, v, x)) {
+                wpx[(size_t)v * W + u] = 0.0f;
+                continue;
+            }
+            double o = orc_mlp_forward(P, x, 1, NULL, NULL);
+            wpx[(size_t)v * W + u] = (float)(1.0 / (1.0 + exp(-o)));
+        }
+}
