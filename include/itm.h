@@ -209,6 +209,58 @@ int itm_scene_import(itm_scene *scene, const int16_t *coords_host, const float *
  * (Sec. 3.2 hashIndex).  Host function, for tools and tests. */
 uint32_t itm_hash_index(int x, int y, int z, int num_buckets);
 
+/* ------------------------------------------------------------------------
+ * Learned per-pixel confidence weight (not in the paper: it replaces the
+ * constant observation weight 1 of the Sec. 4.3 listing through
+ * itm_integrate_weighted).  Features of pixel (u, v): the 7x7 depth patch,
+ * entry (i, j) at index (i+3)*7 + (j+3) = clamp((D(u+j, v+i) - D(u, v))/mu,
+ * -4, 4) where that pixel is inside the image with depth > 0, else 0; then
+ * the camera-facing unit normal of the back-projected depth from central
+ * differences (0 when a neighbour is missing).  Network: h1 = relu(W1 x + b1),
+ * h2 = relu(W2 h1 + b2) (64 each), w_px = sigmoid(w3 . h2 + b3); 0 for pixels
+ * without depth.  Parameters: fp32, ITM_MLP_PARAMS values in the order
+ * W1[64][52], b1[64], W2[64][64], b2[64], w3[64], b3.
+ * ---------------------------------------------------------------------- */
+#define ITM_MLP_FEATURES 52
+#define ITM_MLP_HIDDEN 64
+#define ITM_MLP_PARAMS 7617
+/* packed inference weights: bf16 W1 (64 x 64, features zero-padded),
+ * bf16 W2 (64 x 64), fp32 b1, b2, w3, b3 (+ 3 floats of padding) */
+#define ITM_MLP_PACKED_BYTES 17168
+/* training scratch, floats per sample */
+#define ITM_MLP_SCRATCH_PER_SAMPLE 257
+
+/* Round the fp32 parameters (device, ITM_MLP_PARAMS floats) into the packed
+ * inference layout (device, ITM_MLP_PACKED_BYTES, 16-byte aligned): bf16
+ * round-to-nearest-even for W1 and W2. */
+int itm_mlp_pack(const float *params_dev, void *packed_dev, itm_stream stream);
+
+/* w_px for every pixel of a depth frame (device float[height*width]) with
+ * the packed network: features in fp32, both hidden layers on the tensor
+ * cores with bf16 operands and fp32 accumulation, output layer in fp32. */
+int itm_conf_weights(const float *depth_dev, const itm_intrinsics *intr, float mu, const void *packed_dev,
+                     float *wpx_dev, itm_stream stream);
+
+/* Features (device float[n][52]) of n pixels given by linear index
+ * u + v * width (device int32[n]); out-of-range indices give zeros. */
+int itm_conf_features(const float *depth_dev, const itm_intrinsics *intr, float mu, const int32_t *pixels_dev,
+                      int n, float *feat_dev, itm_stream stream);
+
+/* Mean binary cross-entropy of the network on n samples (features
+ * float[n][52], labels float[n] in {0, 1}, device) into *loss_dev and its
+ * gradient into grad_dev (ITM_MLP_PARAMS floats); the forward rounds W1, W2
+ * and the layer inputs to bf16 exactly as itm_conf_weights does, and the
+ * gradient treats that rounding as the identity.  scratch_dev: device float
+ * [n][ITM_MLP_SCRATCH_PER_SAMPLE] owned by the caller. */
+int itm_mlp_loss_grad(const float *params_dev, const float *feat_dev, const float *labels_dev, int n,
+                      float *scratch_dev, float *grad_dev, float *loss_dev, itm_stream stream);
+
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, bias-corrected for step
+ * >= 1) on the fp32 parameters, with moments m_dev, v_dev (device,
+ * ITM_MLP_PARAMS floats each, zero before step 1). */
+int itm_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int step, float lr,
+                 itm_stream stream);
+
 /* Library version string. */
 const char *itm_version(void);
 

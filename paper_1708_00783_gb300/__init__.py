@@ -23,6 +23,8 @@ ITM_OK = 0
 ERRORS = {1: "ITM_ERR_ARG", 2: "ITM_ERR_CUDA", 3: "ITM_ERR_HASH_FULL", 4: "ITM_ERR_VBA_FULL",
           5: "ITM_ERR_RANGE", 6: "ITM_ERR_TIMEOUT", 7: "ITM_ERR_OVERFLOW", 8: "ITM_ERR_TOO_LARGE"}
 ITM_NOALLOC_MAX_BLOCKS = 1 << 21
+ITM_MLP_FEATURES, ITM_MLP_HIDDEN, ITM_MLP_PARAMS = 52, 64, 7617
+ITM_MLP_PACKED_BYTES, ITM_MLP_SCRATCH_PER_SAMPLE = 17168, 257
 ST_HASH_FULL, ST_VBA_FULL, ST_RANGE, ST_TIMEOUT, ST_OVERFLOW = 0x1, 0x2, 0x4, 0x8, 0x10
 
 
@@ -59,6 +61,7 @@ EXPORTED = [
     "itm_integrate_weighted", "itm_raycast", "itm_process_frame", "itm_depth_u16_to_f32",
     "itm_scene_stats", "itm_scene_status", "itm_scene_export", "itm_scene_export_table",
     "itm_scene_import", "itm_hash_index", "itm_version", "itm_frame_blocks_noalloc", "itm_raycast_range",
+    "itm_mlp_pack", "itm_conf_weights", "itm_conf_features", "itm_mlp_loss_grad", "itm_mlp_adam",
 ]
 
 
@@ -89,6 +92,11 @@ def _load():
         "itm_version": (ctypes.c_char_p, []),
         "itm_frame_blocks_noalloc": (I, [P, ip, fp16, F, F, F, F, P, I, P, P]),
         "itm_raycast_range": (I, [P, ip, fp16, P, P, P]),
+        "itm_mlp_pack": (I, [P, P, P]),
+        "itm_conf_weights": (I, [P, ip, F, P, P, P]),
+        "itm_conf_features": (I, [P, ip, F, P, I, P, P]),
+        "itm_mlp_loss_grad": (I, [P, P, P, I, P, P, P, P]),
+        "itm_mlp_adam": (I, [P, P, P, P, I, F, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -257,6 +265,30 @@ def itm_frame_blocks_noalloc(depth, intr, T_wc, voxel_size, mu, z_min, z_max, co
     _check(_lib.itm_frame_blocks_noalloc(_ptr(depth), ctypes.byref(intr), p, float(voxel_size), float(mu),
                                          float(z_min), float(z_max), _ptr(coords), int(cap), _ptr(count),
                                          _stream(stream)), "itm_frame_blocks_noalloc")
+
+
+def itm_mlp_pack(params, packed, stream=None):
+    _check(_lib.itm_mlp_pack(_ptr(params), _ptr(packed), _stream(stream)), "itm_mlp_pack")
+
+
+def itm_conf_weights(depth, intr, mu, packed, wpx, stream=None):
+    _check(_lib.itm_conf_weights(_ptr(depth), ctypes.byref(intr), float(mu), _ptr(packed), _ptr(wpx),
+                                 _stream(stream)), "itm_conf_weights")
+
+
+def itm_conf_features(depth, intr, mu, pixels, n, feat, stream=None):
+    _check(_lib.itm_conf_features(_ptr(depth), ctypes.byref(intr), float(mu), _ptr(pixels), int(n), _ptr(feat),
+                                  _stream(stream)), "itm_conf_features")
+
+
+def itm_mlp_loss_grad(params, feat, labels, n, scratch, grad, loss, stream=None):
+    _check(_lib.itm_mlp_loss_grad(_ptr(params), _ptr(feat), _ptr(labels), int(n), _ptr(scratch), _ptr(grad),
+                                  _ptr(loss), _stream(stream)), "itm_mlp_loss_grad")
+
+
+def itm_mlp_adam(params, grad, m, v, step, lr, stream=None):
+    _check(_lib.itm_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), _stream(stream)),
+           "itm_mlp_adam")
 
 
 # ------------------------------------------------------------ convenience

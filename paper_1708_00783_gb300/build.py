@@ -34,6 +34,7 @@ SOURCES = {
     "itm_raycast.cu": ["-fmad=false"],
     "itm_depth.cu": ["-fmad=false"],
     "itm_noalloc.cu": ["-fmad=false"],
+    "itm_conf.cu": [],
 }
 
 

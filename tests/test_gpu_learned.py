@@ -1,0 +1,204 @@
+"""Learned confidence weight on the GPU against the oracle, and what it gains.
+
+* features of sampled pixels: |GPU - oracle| <= 1e-4 (fp32 vs fp64);
+* w_px maps (tensor cores, bf16 operands, fp32 accumulation) against the
+  oracle's fp64 forward with the same bf16 rounding: max |d| <= 1e-2, median
+  <= 1e-4 (a bf16 rounding of an input or hidden unit that lands on the other
+  side of a rounding boundary moves the output by well under 1e-2);
+* loss and gradient of a batch: relative error of the gradient <= 1e-2;
+* a short training run lowers the loss;
+* fusing a noisy sequence with the trained weight gives a lower RMS TSDF
+  error against the analytic SDF than the constant weight.
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from synth import kinect_workload, tiny_workload
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def itm():
+    import torch
+    assert torch.cuda.is_available()
+    import paper_1708_00783_gb300 as m
+    return m
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def intr_of(m, intr):
+    return m.make_intrinsics(intr.width, intr.height, intr.fx, intr.fy, intr.cx, intr.cy)
+
+
+def random_params(seed, scale=0.15):
+    rng = np.random.default_rng(seed)
+    p = (rng.normal(size=oracle.N_PARAMS) * scale).astype(np.float32)
+    p[-1] = 1.0
+    return p
+
+
+def test_features_match_oracle(itm):
+    import torch
+    w = kinect_workload()
+    f = w.frame(3)
+    mu = w.params["mu"]
+    rng = np.random.default_rng(0)
+    H, W = f.depth.shape
+    pix = rng.integers(0, H * W, size=3000).astype(np.int32)
+    pix[:4] = [0, W - 1, H * W - 1, (H // 2) * W]       # corners and an edge column
+    out = torch.empty((pix.size, 52), dtype=torch.float32, device="cuda")
+    itm.itm_conf_features(dev(f.depth), intr_of(itm, w.intr), mu, dev(pix), pix.size, out)
+    g = out.cpu().numpy()
+    for s, p in enumerate(pix):
+        x, _ = oracle.conf_features(f.depth, w.intr.as_array(), mu, p % W, p // W)
+        assert np.max(np.abs(g[s] - x)) <= 1e-4, (s, p)
+
+
+@pytest.mark.parametrize("which", ["tiny", "kinect"])
+def test_weight_map_matches_oracle(itm, which):
+    import torch
+    w = tiny_workload() if which == "tiny" else kinect_workload()
+    f = w.frame(2)
+    mu = w.params["mu"]
+    P = random_params(3)
+    model_p = dev(P)
+    packed = torch.zeros(itm.ITM_MLP_PACKED_BYTES, dtype=torch.uint8, device="cuda")
+    itm.itm_mlp_pack(model_p, packed)
+    wpx = torch.full(f.depth.shape, -1.0, dtype=torch.float32, device="cuda")
+    itm.itm_conf_weights(dev(f.depth), intr_of(itm, w.intr), mu, packed, wpx)
+    g = wpx.cpu().numpy()
+    o = oracle.conf_weights(f.depth, w.intr.as_array(), mu, P)
+    d = np.abs(g - o)
+    assert np.all(g[f.depth <= 0] == 0.0)
+    assert d.max() <= 1e-2 and np.median(d[f.depth > 0]) <= 1e-4, (d.max(), np.median(d))
+    assert 0.0 < g[f.depth > 0].min() and g.max() < 1.0
+
+
+def test_loss_and_gradient_match_oracle(itm):
+    import torch
+    rng = np.random.default_rng(5)
+    n = 512
+    X = rng.normal(size=(n, 52)).astype(np.float32)
+    X[:, 49:] /= np.linalg.norm(X[:, 49:], axis=1, keepdims=True)
+    y = (rng.uniform(size=n) > 0.3).astype(np.float32)
+    P = random_params(7)
+    grad = torch.zeros(oracle.N_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    scratch = torch.zeros(n * itm.ITM_MLP_SCRATCH_PER_SAMPLE, dtype=torch.float32, device="cuda")
+    itm.itm_mlp_loss_grad(dev(P), dev(X), dev(y), n, scratch, grad, loss)
+    torch.cuda.synchronize()
+    lo, go = oracle.mlp_loss_grad(P, X.astype(np.float64), y, round_bf16=True)
+    gg = grad.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() - lo) <= 1e-4 * max(1.0, abs(lo))
+    rel = np.linalg.norm(gg - go) / np.linalg.norm(go)
+    assert rel <= 1e-2, rel
+
+
+def _training_set(itm, n_total=200_000, seed=11):
+    from paper_1708_00783_gb300 import learned
+    from synth import confidence
+    frames = confidence.training_frames()
+    rng = np.random.default_rng(seed)
+    w0 = frames[0][0]
+    per = n_total // len(frames)
+    depths, pix, labels = [], [], []
+    for w, f in frames:
+        lab, _ = confidence.pixel_labels(f)
+        depths.append(f.depth)
+        pix.append(confidence.sample_pixels(f, per, rng))
+        labels.append(lab)
+    feat, lab = learned.build_training_set(depths, intr_of(itm, w0.intr), w0.params["mu"], pix, labels)
+    return feat, lab
+
+
+@pytest.fixture(scope="module")
+def trained(itm):
+    from paper_1708_00783_gb300 import learned
+    feat, lab = _training_set(itm)
+    model = learned.ConfidenceModel(seed=0)
+    losses = model.train(feat, lab, steps=400, batch=8192, lr=3e-3)
+    return model, losses, feat, lab
+
+
+@pytest.mark.slow
+def test_training_lowers_the_loss(trained):
+    model, losses, feat, lab = trained
+    assert feat.shape[0] == 199_992 or feat.shape[0] >= 190_000
+    first, last = np.mean(losses[:10]), np.mean(losses[-10:])
+    assert last < 0.8 * first, (first, last)
+    # the trained network separates the labels: mean weight of good pixels
+    # above that of bad ones
+    import torch
+    model.loss_grad(feat[:8192].contiguous(), lab[:8192].contiguous())
+    assert np.isfinite(model.loss.item())
+
+
+def _fuse(itm, w, frames, model=None):
+    """Constant-weight fusion (model None) or learned-weight fusion."""
+    import torch
+    p = dict(w.params)
+    if model is not None:
+        p["weight_mode"] = 1
+    sc = itm.Scene(**p)
+    ci = intr_of(itm, w.intr)
+    wpx = torch.empty((w.intr.height, w.intr.width), dtype=torch.float32, device="cuda")
+    for k in frames:
+        f = w.frame(k)
+        d = dev(f.depth)
+        sc.allocate(d, ci, f.T_wc)
+        if model is None:
+            sc.integrate(d, ci, f.T_wc)
+        else:
+            model.weights(d, ci, p["mu"], wpx)
+            sc.integrate(d, ci, f.T_wc, wpx=wpx)
+    assert sc.status() == 0
+    return sc.export()
+
+
+def rms_tsdf_error(w, exported, keep=None):
+    """RMS of (F mu - SDF) over observed voxels within mu of a surface, with
+    SDF the analytic signed distance at the voxel position."""
+    coords, F, Wt = exported
+    s = float(np.float32(w.params["voxel_size"]))
+    mu = w.params["mu"]
+    l = np.arange(512)
+    local = np.stack([l % 8, (l // 8) % 8, l // 64], axis=1)
+    g = coords.astype(np.int64)[:, None, :] * 8 + local[None]
+    p = g.reshape(-1, 3).astype(np.float64) * s
+    sdf = w.scene.sdf(p).reshape(F.shape)
+    m = (Wt > 0) & (np.abs(sdf) < mu)
+    if keep is not None:
+        m &= keep
+    return float(np.sqrt(np.mean((F[m] * mu - sdf[m]) ** 2))), m
+
+
+@pytest.mark.slow
+def test_learned_weight_lowers_tsdf_error(itm, trained):
+    """Fuse 30 noisy frames (with flying pixels) of a room that was not used
+    for training, once with the constant weight and once with the trained
+    network's weight; compare the RMS TSDF error against the analytic SDF
+    on the voxels both observed."""
+    model, _, _, _ = trained
+    w = kinect_workload(seed=7)
+    frames = range(0, 60, 2)
+    const = _fuse(itm, w, frames)
+    learned_ = _fuse(itm, w, frames, model)
+    key = lambda c: {tuple(x) for x in c.tolist()}
+    assert key(const[0]) == key(learned_[0])      # same allocation
+    order_c = np.lexsort(const[0].T[::-1])
+    order_l = np.lexsort(learned_[0].T[::-1])
+    const = tuple(a[order_c] for a in const)
+    learned_ = tuple(a[order_l] for a in learned_)
+    both = (const[2] > 0) & (learned_[2] > 0)
+    rc, mc = rms_tsdf_error(w, const, both)
+    rl, ml = rms_tsdf_error(w, learned_, both)
+    print("RMS TSDF error: constant %.5f m, learned %.5f m over %d voxels" % (rc, rl, int(mc.sum())))
+    assert mc.sum() > 100_000
+    assert rl < rc, (rl, rc)
