@@ -261,6 +261,54 @@ int itm_mlp_loss_grad(const float *params_dev, const float *feat_dev, const floa
 int itm_mlp_adam(float *params_dev, const float *grad_dev, float *m_dev, float *v_dev, int step, float lr,
                  itm_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Batches (InfiniTAM v3 Sec. 7.2 submaps; many independent scenes).  A batch
+ * runs one frame for each of up to max_items (scene, frame) items through
+ * allocation, integration and raycast with one launch per stage for the whole
+ * batch; each scene gets exactly the arithmetic of itm_process_frame.  The
+ * launches are persistent kernels whose sizes do not depend on the items, so
+ * with a non-NULL stream they are captured into a CUDA graph on the first run
+ * and replayed afterwards (itm_batch_set_graph(b, 0) turns this off).
+ * ---------------------------------------------------------------------- */
+typedef struct itm_batch itm_batch;
+
+/* One item: a frame for one scene.  For a submap, T_wc is the camera pose in
+ * that submap's frame (the world-to-submap transform times the camera's
+ * world pose).  depth_dev may be shared by several items.  vertex_dev and
+ * normal_dev (device float4[height*width], 16-byte aligned) receive the
+ * raycast from T_wc; both NULL skips the raycast for the item. */
+typedef struct {
+    itm_scene *scene;
+    const float *depth_dev;
+    itm_intrinsics intr;
+    float T_wc[16];
+    float *vertex_dev;
+    float *normal_dev;
+} itm_batch_item;
+
+/* Number of tunable batch stages: enumerate, commit, visible list,
+ * integrate, search range, raycast. */
+#define ITM_BATCH_STAGES 6
+
+/* Create a batch for up to max_items (1..256) items on the current device:
+ * device item table, pinned upload ring, default launch shapes.  Errors:
+ * ITM_ERR_ARG, ITM_ERR_CUDA. */
+int itm_batch_create(int max_items, itm_batch **out);
+int itm_batch_destroy(itm_batch *batch);
+
+/* Run one frame for each of the n items (host array, read before the call
+ * returns).  All scenes must be distinct, in weight_mode 0, with images of
+ * at most 4096 x 4096.  Asynchronous on `stream`; up to 4 runs may be in
+ * flight before a call waits for the oldest upload. */
+int itm_batch_run(itm_batch *batch, const itm_batch_item *items, int n, itm_stream stream);
+
+/* CTAs per SM for each of the ITM_BATCH_STAGES persistent stages (0: as many
+ * as fit); drops the captured graph.  itm_batch_get_tuning returns the grid
+ * sizes in use. */
+int itm_batch_set_tuning(itm_batch *batch, const int *ctas_per_sm, int n);
+int itm_batch_get_tuning(itm_batch *batch, int *grid_ctas, int n);
+int itm_batch_set_graph(itm_batch *batch, int use_graph);
+
 /* Library version string. */
 const char *itm_version(void);
 

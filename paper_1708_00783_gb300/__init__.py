@@ -25,6 +25,7 @@ ERRORS = {1: "ITM_ERR_ARG", 2: "ITM_ERR_CUDA", 3: "ITM_ERR_HASH_FULL", 4: "ITM_E
 ITM_NOALLOC_MAX_BLOCKS = 1 << 21
 ITM_MLP_FEATURES, ITM_MLP_HIDDEN, ITM_MLP_PARAMS = 52, 64, 7617
 ITM_MLP_PACKED_BYTES, ITM_MLP_SCRATCH_PER_SAMPLE = 17168, 257
+ITM_BATCH_STAGES = 6
 ST_HASH_FULL, ST_VBA_FULL, ST_RANGE, ST_TIMEOUT, ST_OVERFLOW = 0x1, 0x2, 0x4, 0x8, 0x10
 
 
@@ -45,6 +46,11 @@ class itm_scene_params(ctypes.Structure):
                 ("z_min", ctypes.c_float), ("z_max", ctypes.c_float), ("weight_mode", ctypes.c_int)]
 
 
+class itm_batch_item(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_void_p), ("depth_dev", ctypes.c_void_p), ("intr", itm_intrinsics),
+                ("T_wc", ctypes.c_float * 16), ("vertex_dev", ctypes.c_void_p), ("normal_dev", ctypes.c_void_p)]
+
+
 class itm_stats(ctypes.Structure):
     _fields_ = [("status", ctypes.c_uint32), ("allocated_blocks", ctypes.c_int32),
                 ("excess_used", ctypes.c_int32), ("visible_blocks", ctypes.c_int32),
@@ -62,6 +68,8 @@ EXPORTED = [
     "itm_scene_stats", "itm_scene_status", "itm_scene_export", "itm_scene_export_table",
     "itm_scene_import", "itm_hash_index", "itm_version", "itm_frame_blocks_noalloc", "itm_raycast_range",
     "itm_mlp_pack", "itm_conf_weights", "itm_conf_features", "itm_mlp_loss_grad", "itm_mlp_adam",
+    "itm_batch_create", "itm_batch_destroy", "itm_batch_run", "itm_batch_set_tuning", "itm_batch_get_tuning",
+    "itm_batch_set_graph",
 ]
 
 
@@ -97,6 +105,12 @@ def _load():
         "itm_conf_features": (I, [P, ip, F, P, I, P, P]),
         "itm_mlp_loss_grad": (I, [P, P, P, I, P, P, P, P]),
         "itm_mlp_adam": (I, [P, P, P, P, I, F, P]),
+        "itm_batch_create": (I, [I, ctypes.POINTER(P)]),
+        "itm_batch_destroy": (I, [P]),
+        "itm_batch_run": (I, [P, ctypes.POINTER(itm_batch_item), I, P]),
+        "itm_batch_set_tuning": (I, [P, ctypes.POINTER(I), I]),
+        "itm_batch_get_tuning": (I, [P, ctypes.POINTER(I), I]),
+        "itm_batch_set_graph": (I, [P, I]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -289,6 +303,52 @@ def itm_mlp_loss_grad(params, feat, labels, n, scratch, grad, loss, stream=None)
 def itm_mlp_adam(params, grad, m, v, step, lr, stream=None):
     _check(_lib.itm_mlp_adam(_ptr(params), _ptr(grad), _ptr(m), _ptr(v), int(step), float(lr), _stream(stream)),
            "itm_mlp_adam")
+
+
+def itm_batch_create(max_items) -> int:
+    h = ctypes.c_void_p()
+    _check(_lib.itm_batch_create(int(max_items), ctypes.byref(h)), "itm_batch_create")
+    return h.value
+
+
+def itm_batch_destroy(batch):
+    _check(_lib.itm_batch_destroy(batch), "itm_batch_destroy")
+
+
+def make_batch_items(items):
+    """items: iterable of (scene handle, depth tensor/pointer, itm_intrinsics,
+    T_wc 4x4, vertex or None, normal or None)."""
+    items = list(items)
+    arr = (itm_batch_item * len(items))()
+    for k, (scene, depth, intr, T, vtx, nrm) in enumerate(items):
+        arr[k].scene = scene
+        arr[k].depth_dev = _ptr(depth)
+        arr[k].intr = intr
+        arr[k].T_wc[:] = [float(x) for x in np.asarray(T, dtype=np.float32).reshape(16)]
+        arr[k].vertex_dev = _ptr(vtx)
+        arr[k].normal_dev = _ptr(nrm)
+    return arr
+
+
+def itm_batch_run(batch, items, stream=None):
+    """items: a ctypes array from make_batch_items, or the tuples it takes."""
+    arr = items if isinstance(items, ctypes.Array) else make_batch_items(items)
+    _check(_lib.itm_batch_run(batch, arr, len(arr), _stream(stream)), "itm_batch_run")
+
+
+def itm_batch_set_tuning(batch, ctas_per_sm):
+    a = (ctypes.c_int * ITM_BATCH_STAGES)(*[int(x) for x in ctas_per_sm])
+    _check(_lib.itm_batch_set_tuning(batch, a, ITM_BATCH_STAGES), "itm_batch_set_tuning")
+
+
+def itm_batch_get_tuning(batch):
+    a = (ctypes.c_int * ITM_BATCH_STAGES)()
+    _check(_lib.itm_batch_get_tuning(batch, a, ITM_BATCH_STAGES), "itm_batch_get_tuning")
+    return list(a)
+
+
+def itm_batch_set_graph(batch, use_graph):
+    _check(_lib.itm_batch_set_graph(batch, int(bool(use_graph))), "itm_batch_set_graph")
 
 
 # ------------------------------------------------------------ convenience

@@ -35,6 +35,7 @@ SOURCES = {
     "itm_depth.cu": ["-fmad=false"],
     "itm_noalloc.cu": ["-fmad=false"],
     "itm_conf.cu": [],
+    "itm_batch.cu": ["-fmad=false"],
 }
 
 

@@ -1,0 +1,449 @@
+// Batched per-frame core: many (scene, frame) items -- rigid submaps that one
+// frame is fused into at their relative poses (InfiniTAM v3 Sec. 7.2), or
+// independent scenes of different sizes -- go through allocation,
+// integration and raycast with one launch per stage for the whole batch.
+//
+// Every stage is a persistent kernel (a fixed number of CTAs per SM) walking
+// one virtual work space that concatenates the items' work: 32x8-pixel tiles
+// for enumeration and raycast (sizes known on the host), and requests,
+// allocated blocks and visible blocks for the other stages, whose per-item
+// counts live on the device and are prefix-summed by each CTA at start.  A
+// virtual index is mapped back to its item by binary search, and the item's
+// work runs through the same bodies as the single-scene kernels (itm_ops.cuh),
+// so each scene gets bit-identical arithmetic.  Because no launch depends on
+// the work sizes, the eight launches are captured once into a CUDA graph and
+// replayed for any item set up to the batch's capacity: per frame the host
+// only uploads the item table (pinned ring buffer, one async copy) and
+// launches the graph.
+//
+// Launch shapes are tunable per stage (CTAs per SM; itm_batch_set_tuning),
+// which is what the autotuner in paper_1708_00783_gb300/autotune.py searches.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "itm_ops.cuh"
+
+namespace itm {
+
+namespace {
+
+constexpr int kMaxItems = 256;
+constexpr int kRing = 4;
+enum Stage { ST_ENUM = 0, ST_COMMIT, ST_VISIBLE, ST_INTEGRATE, ST_RANGE, ST_RAYCAST, ST_COUNT };
+
+struct ItemDev {
+    SceneDev s;
+    const float *depth;
+    float4 *vtx, *nrm;
+    Intr in;
+    Mat34 T, M;
+    float inv_b, tB_m, inv_sv, zc;
+    int max_iter;
+    int cta_tiles_x;  // 32x8-pixel tiles per row
+    int cta_begin;    // first virtual 32x8 tile of this item
+    int rtiles_x, rtiles_y;
+    int raycast;
+};
+
+struct BatchHead {
+    int n, cta_total, pad0, pad1;
+};
+
+// last index i in [0, n) with prefix[i] <= v (prefix ascending, prefix[0] = 0)
+__device__ __forceinline__ int find_item(const int *prefix, int n, int v)
+{
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (prefix[mid] <= v) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// prefix[i] = sum of count(item j) for j < i, prefix[n] = total (whole CTA)
+template <class Count>
+__device__ __forceinline__ int cta_prefix(const ItemDev *__restrict__ items, int n, int *prefix, Count count)
+{
+    for (int i = threadIdx.x; i < n; i += blockDim.x) prefix[i + 1] = count(items[i]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        prefix[0] = 0;
+        for (int i = 1; i <= n; ++i) prefix[i] += prefix[i - 1];
+    }
+    __syncthreads();
+    return prefix[n];
+}
+
+__global__ void __launch_bounds__(256) batch_begin_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
+{
+    const int n = head->n;
+    if ((int)blockIdx.x >= n) return;
+    const ItemDev &it = items[blockIdx.x];
+    if (threadIdx.x < kFrameCountersBytes / 4)
+        reinterpret_cast<int *>(reinterpret_cast<char *>(it.s.ctr) + kFrameCountersOffset)[threadIdx.x] = 0;
+    const int tiles = it.rtiles_x * it.rtiles_y;
+    for (int i = threadIdx.x; i < tiles; i += blockDim.x) {
+        it.s.range_min[i] = 0xffffffffu;
+        it.s.range_max[i] = 0u;
+    }
+}
+
+__global__ void __launch_bounds__(256) batch_enumerate_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
+{
+    __shared__ int begin[kMaxItems + 1];
+    const int n = head->n, total = head->cta_total;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) begin[i] = items[i].cta_begin;
+    __syncthreads();
+    for (int vt = blockIdx.x; vt < total; vt += gridDim.x) {
+        const int k = find_item(begin, n, vt);
+        const ItemDev &it = items[k];
+        const int local = vt - begin[k];
+        enumerate_tile(it.s, it.depth, it.in, it.T, it.inv_b, local % it.cta_tiles_x, local / it.cta_tiles_x);
+    }
+}
+
+__global__ void __launch_bounds__(256) batch_commit_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
+{
+    __shared__ int prefix[kMaxItems + 1];
+    const int n = head->n;
+    const int total = cta_prefix(items, n, prefix, [](const ItemDev &it) {
+        return min(__ldcg(&it.s.ctr->n_req), it.s.nb);
+    });
+    for (int i0 = blockIdx.x * blockDim.x; i0 < total; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        if (i >= total) continue;
+        const int k = find_item(prefix, n, i);
+        commit_request(items[k].s, i - prefix[k]);
+    }
+}
+
+__global__ void __launch_bounds__(kOvfThreads) batch_overflow_kernel(const ItemDev *__restrict__ items,
+                                                                     const BatchHead *head)
+{
+    __shared__ int remaining;
+    if ((int)blockIdx.x >= head->n) return;
+    overflow_scene(items[blockIdx.x].s, remaining);
+}
+
+__global__ void __launch_bounds__(256) batch_visible_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
+{
+    __shared__ int prefix[kMaxItems + 1];
+    const int n = head->n;
+    const int total = cta_prefix(items, n, prefix, [](const ItemDev &it) {
+        return min(__ldcg(&it.s.ctr->block_head), it.s.nv);
+    });
+    for (int i0 = blockIdx.x * blockDim.x; i0 < total; i0 += gridDim.x * blockDim.x) {
+        const int i = i0 + threadIdx.x;
+        if (i >= total) continue;
+        const int k = find_item(prefix, n, i);
+        const ItemDev &it = items[k];
+        visible_block(it.s, it.M, it.in, visible_zfar(it.s), i - prefix[k]);
+    }
+}
+
+__global__ void __launch_bounds__(64) batch_integrate_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
+{
+    __shared__ int prefix[kMaxItems + 1];
+    const int n = head->n;
+    const int total = cta_prefix(items, n, prefix, [](const ItemDev &it) {
+        return min(__ldcg(&it.s.ctr->n_visible), it.s.nv);
+    });
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        for (int k = 0; k < n; ++k) {
+            atomicAdd(&items[k].s.ctr->visited, (unsigned long long)(prefix[k + 1] - prefix[k]) * kBlockVoxels);
+            atomicAdd(&items[k].s.ctr->frames, 1ull);
+        }
+    }
+    const int t = threadIdx.x;
+    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+        const int k = find_item(prefix, n, vb);
+        const ItemDev &it = items[k];
+        const int ptr = __ldg(&it.s.visible[vb - prefix[k]]);
+        const short4 b = __ldg(&it.s.block_pos[ptr]);
+        unsigned updated = 0;
+        short4 unused = b;
+        integrate_block<0>(it.s, it.depth, nullptr, it.in, it.M, ptr, b, t, updated, false, 0, unused);
+        for (int o = 16; o > 0; o >>= 1) updated += __shfl_xor_sync(kFull, updated, o);
+        if ((t & 31) == 0 && updated) atomicAdd(&it.s.ctr->updated, (unsigned long long)updated);
+    }
+}
+
+__global__ void __launch_bounds__(256) batch_range_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
+{
+    __shared__ int prefix[kMaxItems + 1];
+    const int n = head->n;
+    // work unit: a chunk of 32 allocated blocks of one item (one warp)
+    const int total = cta_prefix(items, n, prefix, [](const ItemDev &it) {
+        return it.raycast ? (min(__ldcg(&it.s.ctr->block_head), it.s.nv) + 31) / 32 : 0;
+    });
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int c = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < total; c += warps) {
+        const int k = find_item(prefix, n, c);
+        const ItemDev &it = items[k];
+        const int nb = min(__ldcg(&it.s.ctr->block_head), it.s.nv);
+        const int i = (c - prefix[k]) * 32 + lane;
+        TileRange r{0, -1, 0, -1, 0.f, 0.f};
+        bool ok = false;
+        if (i < nb) {
+            const int ptr = __ldg(&it.s.block_free[i]);
+            const short4 b = __ldg(&it.s.block_pos[ptr]);
+            if (b.w) ok = block_tile_range(b, it.M, it.in, it.s.voxel_size, it.zc, it.rtiles_x, it.rtiles_y, r);
+        }
+        range_rasterize(ok, r, it.rtiles_x, it.s.range_min, it.s.range_max);
+    }
+}
+
+__global__ void __launch_bounds__(256) batch_raycast_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
+{
+    __shared__ int begin[kMaxItems + 1];
+    const int n = head->n, total = head->cta_total;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) begin[i] = items[i].cta_begin;
+    __syncthreads();
+    for (int vt = blockIdx.x; vt < total; vt += gridDim.x) {
+        const int k = find_item(begin, n, vt);
+        const ItemDev &it = items[k];
+        if (!it.raycast) continue;
+        const int local = vt - begin[k];
+        raycast_tile<0, true>(it.s, it.in, it.T, it.vtx, it.nrm, it.max_iter, it.tB_m, it.inv_sv, it.s.range_min,
+                              it.s.range_max, it.rtiles_x, it.rtiles_y, local % it.cta_tiles_x,
+                              local / it.cta_tiles_x);
+    }
+}
+
+const void *stage_kernel(int st)
+{
+    switch (st) {
+    case ST_ENUM: return (const void *)batch_enumerate_kernel;
+    case ST_COMMIT: return (const void *)batch_commit_kernel;
+    case ST_VISIBLE: return (const void *)batch_visible_kernel;
+    case ST_INTEGRATE: return (const void *)batch_integrate_kernel;
+    case ST_RANGE: return (const void *)batch_range_kernel;
+    default: return (const void *)batch_raycast_kernel;
+    }
+}
+
+const int kStageThreads[ST_COUNT] = {256, 256, 256, 64, 256, 256};
+
+}  // namespace
+
+}  // namespace itm
+
+using namespace itm;
+
+struct itm_batch {
+    int max_items;
+    ItemDev *d_items;
+    BatchHead *d_head;
+    unsigned char *h_stage[kRing];
+    cudaEvent_t ev[kRing];
+    int ring;
+    int sms;
+    int per_sm[ST_COUNT];  // 0: as many as fit
+    int grid[ST_COUNT];
+    int use_graph;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int have_graph;
+};
+
+static void batch_grids(itm_batch *b)
+{
+    for (int st = 0; st < ST_COUNT; ++st) {
+        int fit = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, stage_kernel(st), kStageThreads[st], 0);
+        if (fit < 1) fit = 1;
+        int per = b->per_sm[st] > 0 && b->per_sm[st] < fit ? b->per_sm[st] : fit;
+        b->grid[st] = b->sms * per;
+    }
+}
+
+static void drop_graph(itm_batch *b)
+{
+    if (b->have_graph) {
+        cudaGraphExecDestroy(b->exec);
+        cudaGraphDestroy(b->graph);
+        b->have_graph = 0;
+    }
+}
+
+static cudaError_t launch_stages(itm_batch *b, cudaStream_t st)
+{
+    const ItemDev *it = b->d_items;
+    const BatchHead *h = b->d_head;
+    batch_begin_kernel<<<b->max_items, 256, 0, st>>>(it, h);
+    batch_enumerate_kernel<<<b->grid[ST_ENUM], 256, 0, st>>>(it, h);
+    batch_commit_kernel<<<b->grid[ST_COMMIT], 256, 0, st>>>(it, h);
+    batch_overflow_kernel<<<b->max_items, kOvfThreads, 0, st>>>(it, h);
+    batch_visible_kernel<<<b->grid[ST_VISIBLE], 256, 0, st>>>(it, h);
+    batch_integrate_kernel<<<b->grid[ST_INTEGRATE], 64, 0, st>>>(it, h);
+    batch_range_kernel<<<b->grid[ST_RANGE], 256, 0, st>>>(it, h);
+    batch_raycast_kernel<<<b->grid[ST_RAYCAST], 256, 0, st>>>(it, h);
+    return cudaGetLastError();
+}
+
+extern "C" {
+
+int itm_batch_create(int max_items, itm_batch **out)
+{
+    if (!out || max_items < 1 || max_items > kMaxItems) return ITM_ERR_ARG;
+    *out = nullptr;
+    itm_batch *b = (itm_batch *)calloc(1, sizeof(itm_batch));
+    if (!b) return ITM_ERR_ARG;
+    b->max_items = max_items;
+    b->use_graph = 1;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (b->sms < 1) b->sms = 1;
+    const size_t stage_bytes = sizeof(BatchHead) + sizeof(ItemDev) * (size_t)max_items;
+    cudaError_t e = cudaMalloc((void **)&b->d_head, stage_bytes);
+    if (e == cudaSuccess) b->d_items = reinterpret_cast<ItemDev *>(b->d_head + 1);
+    for (int r = 0; r < kRing && e == cudaSuccess; ++r) {
+        e = cudaMallocHost((void **)&b->h_stage[r], stage_bytes);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev[r], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess) {
+        cudaMemset(b->d_head, 0, sizeof(BatchHead));
+        batch_grids(b);
+        e = cudaDeviceSynchronize();
+    }
+    if (e != cudaSuccess) {
+        for (int r = 0; r < kRing; ++r) {
+            if (b->h_stage[r]) cudaFreeHost(b->h_stage[r]);
+            if (b->ev[r]) cudaEventDestroy(b->ev[r]);
+        }
+        if (b->d_head) cudaFree(b->d_head);
+        free(b);
+        cudaGetLastError();
+        return ITM_ERR_CUDA;
+    }
+    *out = b;
+    return ITM_OK;
+}
+
+int itm_batch_destroy(itm_batch *b)
+{
+    if (!b) return ITM_ERR_ARG;
+    cudaDeviceSynchronize();
+    drop_graph(b);
+    for (int r = 0; r < kRing; ++r) {
+        cudaFreeHost(b->h_stage[r]);
+        cudaEventDestroy(b->ev[r]);
+    }
+    cudaFree(b->d_head);
+    free(b);
+    return ITM_OK;
+}
+
+int itm_batch_set_tuning(itm_batch *b, const int *ctas_per_sm, int n)
+{
+    if (!b || !ctas_per_sm || n != ST_COUNT) return ITM_ERR_ARG;
+    for (int i = 0; i < n; ++i)
+        if (ctas_per_sm[i] < 0 || ctas_per_sm[i] > 64) return ITM_ERR_ARG;
+    cudaDeviceSynchronize();
+    for (int i = 0; i < n; ++i) b->per_sm[i] = ctas_per_sm[i];
+    batch_grids(b);
+    drop_graph(b);
+    return ITM_OK;
+}
+
+int itm_batch_get_tuning(itm_batch *b, int *grid_ctas, int n)
+{
+    if (!b || !grid_ctas || n != ST_COUNT) return ITM_ERR_ARG;
+    for (int i = 0; i < n; ++i) grid_ctas[i] = b->grid[i];
+    return ITM_OK;
+}
+
+int itm_batch_set_graph(itm_batch *b, int use_graph)
+{
+    if (!b) return ITM_ERR_ARG;
+    cudaDeviceSynchronize();
+    b->use_graph = use_graph ? 1 : 0;
+    drop_graph(b);
+    return ITM_OK;
+}
+
+int itm_batch_run(itm_batch *b, const itm_batch_item *items, int n, itm_stream stream)
+{
+    if (!b || n < 1 || n > b->max_items || !items) return ITM_ERR_ARG;
+    // validate everything before touching the device
+    for (int i = 0; i < n; ++i) {
+        const itm_batch_item &x = items[i];
+        if (!x.scene || !x.depth_dev || !valid_intr(&x.intr)) return ITM_ERR_ARG;
+        if (x.scene->d.weight_mode != 0) return ITM_ERR_ARG;
+        if (x.intr.width > kRangeMaxW || x.intr.height > kRangeMaxH) return ITM_ERR_ARG;
+        if ((x.vertex_dev != nullptr) != (x.normal_dev != nullptr)) return ITM_ERR_ARG;
+        if ((reinterpret_cast<uintptr_t>(x.vertex_dev) & 15) || (reinterpret_cast<uintptr_t>(x.normal_dev) & 15))
+            return ITM_ERR_ARG;
+        for (int k = 0; k < 16; ++k)
+            if (!isfinite(x.T_wc[k])) return ITM_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (items[j].scene == x.scene) return ITM_ERR_ARG;  // one frame per scene per batch
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int slot = b->ring;
+    b->ring = (b->ring + 1) % kRing;
+    if (cudaEventSynchronize(b->ev[slot]) != cudaSuccess) return ITM_ERR_CUDA;  // the slot's last copy is done
+    BatchHead *h = reinterpret_cast<BatchHead *>(b->h_stage[slot]);
+    ItemDev *it = reinterpret_cast<ItemDev *>(h + 1);
+    int cta_total = 0;
+    for (int i = 0; i < n; ++i) {
+        const itm_batch_item &x = items[i];
+        ItemDev &d = it[i];
+        memset(&d, 0, sizeof(d));
+        d.s = x.scene->d;
+        d.depth = x.depth_dev;
+        d.vtx = reinterpret_cast<float4 *>(x.vertex_dev);
+        d.nrm = reinterpret_cast<float4 *>(x.normal_dev);
+        d.raycast = x.vertex_dev != nullptr;
+        d.in = to_intr(&x.intr);
+        pose_rows(x.T_wc, d.T);
+        rigid_inverse_rows(x.T_wc, d.M);
+        const SceneDev &s = x.scene->d;
+        d.inv_b = (float)(1.0 / (8.0 * (double)s.voxel_size));
+        // the same host-side float steps as launch_raycast
+        volatile float span = s.z_max - s.z_min;
+        volatile float four_span = 4.0f * span;
+        volatile float ratio = four_span / s.voxel_size;
+        d.max_iter = (int)ratio + 64;
+        volatile float tB_m = 8.0f * s.voxel_size;
+        d.tB_m = tB_m;
+        d.inv_sv = (float)(1.0 / (double)s.voxel_size);
+        d.zc = s.z_min - 1e-3f;
+        d.cta_tiles_x = (x.intr.width + 31) / 32;
+        d.cta_begin = cta_total;
+        cta_total += d.cta_tiles_x * ((x.intr.height + 7) / 8);
+        d.rtiles_x = (x.intr.width + 7) / 8;
+        d.rtiles_y = (x.intr.height + 3) / 4;
+    }
+    h->n = n;
+    h->cta_total = cta_total;
+    h->pad0 = h->pad1 = 0;
+    cudaError_t e = cudaMemcpyAsync(b->d_head, h, sizeof(BatchHead) + sizeof(ItemDev) * (size_t)n,
+                                    cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], st);
+    if (e != cudaSuccess) return ITM_ERR_CUDA;
+    if (b->use_graph && st != nullptr) {
+        if (!b->have_graph) {
+            e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e == cudaSuccess) {
+                cudaError_t le = launch_stages(b, st);
+                e = cudaStreamEndCapture(st, &b->graph);
+                if (e == cudaSuccess) e = le;
+            }
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+            if (e != cudaSuccess) return ITM_ERR_CUDA;
+            b->have_graph = 1;
+        }
+        e = cudaGraphLaunch(b->exec, st);
+    } else {
+        e = launch_stages(b, st);
+    }
+    for (int i = 0; i < n; ++i) items[i].scene->last_stream = st;
+    return check_cuda(e);
+}
+
+}  // extern "C"

@@ -164,16 +164,18 @@ __device__ __forceinline__ void set_status(const SceneDev &s, uint32_t bits)
 }
 
 // Warp-aggregated append: the lanes active at the call each get a distinct
-// slot; one atomic per warp.
+// slot of their counter; lanes naming the same counter share one atomic
+// (lanes of one warp may work for different scenes in a batch).
 __device__ __forceinline__ int warp_append(int32_t *counter)
 {
-    const unsigned m = __activemask();
+    const unsigned active = __activemask();
     const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
+    const unsigned peers = __match_any_sync(active, (unsigned long long)counter);
+    const int leader = __ffs(peers) - 1;
     int base = 0;
-    if (lane == leader) base = atomicAdd(counter, __popc(m));
-    base = __shfl_sync(m, base, leader);
-    return base + __popc(m & ((1u << lane) - 1u));
+    if (lane == leader) base = atomicAdd(counter, __popc(peers));
+    base = __shfl_sync(active, base, leader);
+    return base + __popc(peers & ((1u << lane) - 1u));
 }
 
 }  // namespace itm

@@ -37,155 +37,13 @@
 // __match_any_sync and one lane per group walks the hash chain (Sec. 3.3),
 // the others take its answer by shuffle.  Every arithmetic step of the march
 // uses IEEE round-to-nearest operations in a fixed order.
-#include "itm_internal.cuh"
+#include "itm_ops.cuh"
 
 namespace itm {
 
 namespace {
 
-enum { COARSE = 0, FINE = 1, SURFACE = 2, BEHIND = 3, WRONG = 4, MISS = 5 };
-
-constexpr float kRangeMarginZ = 1e-4f;  // metres, covers rounding of p(t) vs t
-constexpr float kRangeMarginPx = 1.0f;  // pixels
-
-__device__ __forceinline__ bool coord_ok(float q) { return q > -262000.0f && q < 262000.0f; }
-__device__ __forceinline__ bool in_i16(int v) { return v >= -32768 && v <= 32767; }
-
-__device__ __forceinline__ float lerp_rn(float a, float b, float t) { return fadd(a, fmul(t, fsub(b, a))); }
-
-// One-entry cache of the last block looked up by this thread.
-struct BlockCache {
-    unsigned long long key;
-    int ptr;
-};
-
-__device__ __forceinline__ int cached_lookup(const SceneDev &s, BlockCache &c, int bx, int by, int bz)
-{
-    if (!(in_i16(bx) && in_i16(by) && in_i16(bz))) return -1;
-    const unsigned long long k = pack_key(bx, by, bz);
-    if (k == c.key) return c.ptr;
-    c.key = k;
-    c.ptr = lookup_ro(s, bx, by, bz);
-    return c.ptr;
-}
-
-template <int MODE, bool OBS>
-__device__ __forceinline__ float voxel_at(const SceneDev &s, int ptr, int gx, int gy, int gz, bool &all_obs)
-{
-    if (ptr < 0) {
-        if (OBS) all_obs = false;
-        return 1.0f;
-    }
-    const size_t i = (size_t)ptr * kBlockVoxels + (gx & 7) + 8 * (gy & 7) + 64 * (gz & 7);
-    if (OBS) {
-        if (MODE == 0) all_obs = all_obs && (__ldg(&s.w8[i]) != 0);
-        else all_obs = all_obs && (__ldg(&s.w32[i]) > 0.0f);
-    }
-    return __ldg(&s.sdf[i]);
-}
-
-// Trilinear interpolation at voxel coordinates (q0, q1, q2).  Each distinct
-// block under the 2x2x2 stencil is looked up once.  With OBS, all_obs is
-// cleared when one of the eight voxels is unallocated or unobserved.
-template <int MODE, bool OBS>
-__device__ __forceinline__ float trilinear(const SceneDev &s, BlockCache &c, float q0, float q1, float q2,
-                                           bool &all_obs)
-{
-    const float g0x = floorf(q0), g0y = floorf(q1), g0z = floorf(q2);
-    const float fx = fsub(q0, g0x), fy = fsub(q1, g0y), fz = fsub(q2, g0z);
-    const int x = (int)g0x, y = (int)g0y, z = (int)g0z;
-    const int bx = x >> 3, by = y >> 3, bz = z >> 3;
-    const bool cx = (x & 7) == 7, cy = (y & 7) == 7, cz = (z & 7) == 7;
-    int P[8];
-    P[0] = cached_lookup(s, c, bx, by, bz);
-    P[1] = cx ? cached_lookup(s, c, bx + 1, by, bz) : P[0];
-    P[2] = cy ? cached_lookup(s, c, bx, by + 1, bz) : P[0];
-    P[3] = cy ? (cx ? cached_lookup(s, c, bx + 1, by + 1, bz) : P[2]) : P[1];
-    P[4] = cz ? cached_lookup(s, c, bx, by, bz + 1) : P[0];
-    P[5] = cz ? (cx ? cached_lookup(s, c, bx + 1, by, bz + 1) : P[4]) : P[1];
-    P[6] = cz ? (cy ? cached_lookup(s, c, bx, by + 1, bz + 1) : P[4]) : P[2];
-    P[7] = cz ? (cy ? (cx ? cached_lookup(s, c, bx + 1, by + 1, bz + 1) : P[6]) : P[5]) : P[3];
-    float cv[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-        cv[k] = voxel_at<MODE, OBS>(s, P[k], x + (k & 1), y + ((k >> 1) & 1), z + ((k >> 2) & 1), all_obs);
-    const float c00 = lerp_rn(cv[0], cv[1], fx);
-    const float c10 = lerp_rn(cv[2], cv[3], fx);
-    const float c01 = lerp_rn(cv[4], cv[5], fx);
-    const float c11 = lerp_rn(cv[6], cv[7], fx);
-    const float c0 = lerp_rn(c00, c10, fy);
-    const float c1 = lerp_rn(c01, c11, fy);
-    return lerp_rn(c0, c1, fz);
-}
-
-// ------------------------------------------------------------ search range
-
-struct TileRange {
-    int tx0, tx1, ty0, ty1;
-    float zlo, zhi;
-};
-
-// Conservative tile rectangle and depth range of block b's query region
-// clipped to z >= zc.  Returns false when the region cannot be met by a ray.
-__device__ bool block_tile_range(short4 b, const Mat34 &M, const Intr &in, float vs, float zc, int tiles_x,
-                                 int tiles_y, TileRange &r)
-{
-    const float eps = 1e-5f;
-    const float lo[3] = {((float)(b.x * 8) - 0.51f) * vs - eps, ((float)(b.y * 8) - 0.51f) * vs - eps,
-                         ((float)(b.z * 8) - 0.51f) * vs - eps};
-    const float hi[3] = {((float)(b.x * 8) + 7.51f) * vs + eps, ((float)(b.y * 8) + 7.51f) * vs + eps,
-                         ((float)(b.z * 8) + 7.51f) * vs + eps};
-    float X[8], Y[8], Z[8];
-    float zmax = -3.0e38f;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const float px = (c & 1) ? hi[0] : lo[0], py = (c & 2) ? hi[1] : lo[1], pz = (c & 4) ? hi[2] : lo[2];
-        X[c] = M.m[0] * px + M.m[1] * py + M.m[2] * pz + M.m[3];
-        Y[c] = M.m[4] * px + M.m[5] * py + M.m[6] * pz + M.m[7];
-        Z[c] = M.m[8] * px + M.m[9] * py + M.m[10] * pz + M.m[11];
-        zmax = fmaxf(zmax, Z[c]);
-    }
-    if (zmax < zc) return false;
-    float umin = 3.0e38f, umax = -3.0e38f, vmin = 3.0e38f, vmax = -3.0e38f, zmin = 3.0e38f;
-    auto add_point = [&](float x, float y, float z) {
-        const float u = in.fx * x / z + in.cx, v = in.fy * y / z + in.cy;
-        umin = fminf(umin, u);
-        umax = fmaxf(umax, u);
-        vmin = fminf(vmin, v);
-        vmax = fmaxf(vmax, v);
-        zmin = fminf(zmin, z);
-    };
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        if (Z[c] >= zc) add_point(X[c], Y[c], Z[c]);
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int d = c | (1 << a);
-            if (d == c) continue;
-            // edge c-d crosses the plane z = zc
-            if ((Z[c] < zc) != (Z[d] < zc)) {
-                const float w = (zc - Z[c]) / (Z[d] - Z[c]);
-                add_point(X[c] + w * (X[d] - X[c]), Y[c] + w * (Y[d] - Y[c]), zc);
-            }
-        }
-    }
-    if (!(umax >= -kRangeMarginPx && vmax >= -kRangeMarginPx && umin <= (float)in.W - 1.0f + kRangeMarginPx &&
-          vmin <= (float)in.H - 1.0f + kRangeMarginPx))
-        return false;
-    const float u0 = fmaxf(umin - kRangeMarginPx, 0.0f), u1 = fminf(umax + kRangeMarginPx, (float)(in.W - 1));
-    const float v0 = fmaxf(vmin - kRangeMarginPx, 0.0f), v1 = fminf(vmax + kRangeMarginPx, (float)(in.H - 1));
-    r.tx0 = min((int)u0 >> 3, tiles_x - 1);
-    r.tx1 = min((int)u1 >> 3, tiles_x - 1);
-    r.ty0 = min((int)v0 >> 2, tiles_y - 1);
-    r.ty1 = min((int)v1 >> 2, tiles_y - 1);
-    r.zlo = fmaxf(zmin - kRangeMarginZ, 0.0f);
-    r.zhi = zmax + kRangeMarginZ;
-    return r.tx0 <= r.tx1 && r.ty0 <= r.ty1;
-}
-
-// One warp takes 32 allocated blocks; their tile rectangles are then
-// rasterised by the whole warp, block after block, with atomic min/max on the
-// float bits (non-negative floats order like their bit patterns).
+// One warp takes 32 allocated blocks and rasterises their tile rectangles.
 __global__ void __launch_bounds__(256) range_kernel(SceneDev s, Mat34 M, Intr in, float zc, int tiles_x,
                                                     int tiles_y, uint32_t *__restrict__ rmin,
                                                     uint32_t *__restrict__ rmax)
@@ -202,25 +60,9 @@ __global__ void __launch_bounds__(256) range_kernel(SceneDev s, Mat34 M, Intr in
             const short4 b = __ldg(&s.block_pos[ptr]);
             if (b.w) ok = block_tile_range(b, M, in, s.voxel_size, zc, tiles_x, tiles_y, r);
         }
-        unsigned todo = __ballot_sync(kFull, ok);
-        while (todo) {
-            const int j = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const int tx0 = __shfl_sync(kFull, r.tx0, j), tx1 = __shfl_sync(kFull, r.tx1, j);
-            const int ty0 = __shfl_sync(kFull, r.ty0, j), ty1 = __shfl_sync(kFull, r.ty1, j);
-            const uint32_t zlo = __float_as_uint(__shfl_sync(kFull, r.zlo, j));
-            const uint32_t zhi = __float_as_uint(__shfl_sync(kFull, r.zhi, j));
-            const int w = tx1 - tx0 + 1, cnt = w * (ty1 - ty0 + 1);
-            for (int k = lane; k < cnt; k += 32) {
-                const int t = (ty0 + k / w) * tiles_x + tx0 + k % w;
-                atomicMin(&rmin[t], zlo);
-                atomicMax(&rmax[t], zhi);
-            }
-        }
+        range_rasterize(ok, r, tiles_x, rmin, rmax);
     }
 }
-
-// ---------------------------------------------------------------- march
 
 template <int MODE, bool RANGE>
 __global__ void __launch_bounds__(256) raycast_kernel(SceneDev s, Intr in, Mat34 T, float4 *__restrict__ vtx,
@@ -228,155 +70,8 @@ __global__ void __launch_bounds__(256) raycast_kernel(SceneDev s, Intr in, Mat34
                                                       float inv_sv, const uint32_t *__restrict__ rmin,
                                                       const uint32_t *__restrict__ rmax, int tiles_x, int tiles_y)
 {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int u = blockIdx.x * 32 + (warp & 3) * 8 + (lane & 7);
-    const int v = blockIdx.y * 8 + (warp >> 2) * 4 + (lane >> 3);
-    const bool inside = u < in.W && v < in.H;
-
-    const float vs = s.voxel_size;
-    float org[3], dir[3];
-    const float dc0 = fdiv(fsub((float)u, in.cx), in.fx);
-    const float dc1 = fdiv(fsub((float)v, in.cy), in.fy);
-    const float len = __fsqrt_rn(fadd(fadd(fmul(dc0, dc0), fmul(dc1, dc1)), 1.0f));
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        dir[i] = fadd(fadd(fmul(T.m[4 * i], dc0), fmul(T.m[4 * i + 1], dc1)), T.m[4 * i + 2]);
-        org[i] = T.m[4 * i + 3];
-    }
-    const float tB = fdiv(tB_m, len), tmu = fdiv(s.mu, len), ts = fdiv(vs, len);
-
-    BlockCache cache{0ull, -1};
-    float t = s.z_min;
-    int state = inside ? COARSE : MISS;
-    int it = 0;
-    float tlo = 0.0f, thi = 3.0e38f;
-    const int tix = blockIdx.x * 4 + (warp & 3), tiy = blockIdx.y * 2 + (warp >> 2);
-    if (RANGE && tix < tiles_x && tiy < tiles_y) {
-        // the warp's pixels form one tile (a tile outside the image has no pixel inside)
-        const int tile = tiy * tiles_x + tix;
-        const uint32_t lo = __ldg(&rmin[tile]), hi = __ldg(&rmax[tile]);
-        if (lo == 0xffffffffu) {
-            tlo = thi = -1.0f;  // no block covers the tile
-        } else {
-            tlo = __uint_as_float(lo);
-            thi = __uint_as_float(hi);
-        }
-        if (state == COARSE) {
-            if (thi < 0.0f) {
-                state = MISS;
-            } else {
-                // the oracle's coarse steps in front of every block: t += tB each
-                while (t < tlo && it < max_iter && t <= s.z_max) {
-                    t = fadd(t, tB);
-                    ++it;
-                }
-            }
-        }
-    }
-    float q[3] = {0.f, 0.f, 0.f};
-
-    while (__any_sync(kFull, state <= SURFACE)) {
-        bool marching = state <= SURFACE;
-        if (marching && !(it < max_iter && t <= s.z_max)) {
-            state = MISS;
-            marching = false;
-        }
-        if (RANGE && marching && state != SURFACE && t > thi) {
-            state = MISS;  // only unallocated space ahead: the march can only miss
-            marching = false;
-        }
-        bool ok = marching;
-        int bx = 0, by = 0, bz = 0;
-        if (marching) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                q[i] = fmul(fadd(org[i], fmul(t, dir[i])), inv_sv);
-                ok = ok && coord_ok(q[i]);
-            }
-            if (ok) {
-                bx = ((int)floorf(fadd(q[0], 0.5f))) >> 3;
-                by = ((int)floorf(fadd(q[1], 0.5f))) >> 3;
-                bz = ((int)floorf(fadd(q[2], 0.5f))) >> 3;
-                ok = in_i16(bx) && in_i16(by) && in_i16(bz);
-            }
-        }
-        // warp-cooperative block query
-        const unsigned long long key = ok ? pack_key(bx, by, bz) : 0ull;
-        const unsigned peers = __match_any_sync(kFull, key);
-        const int leader = __ffs(peers) - 1;
-        int ptr = -1;
-        if (ok && lane == leader) ptr = (key == cache.key) ? cache.ptr : lookup_ro(s, bx, by, bz);
-        ptr = __shfl_sync(kFull, ptr, leader);
-        if (ok) {
-            cache.key = key;
-            cache.ptr = ptr;
-        }
-        if (!marching) continue;
-        ++it;
-        const bool alloc = ok && ptr >= 0;
-        if (state == COARSE) {
-            if (!alloc) {
-                t = fadd(t, tB);
-            } else {
-                t = fsub(t, tB);
-                state = FINE;
-            }
-            continue;
-        }
-        if (!alloc) {
-            if (state == FINE) t = fadd(t, tmu);
-            else state = COARSE;
-            continue;
-        }
-        bool unused = true;
-        const float F = trilinear<MODE, false>(s, cache, q[0], q[1], q[2], unused);
-        if (state == FINE) {
-            if (F <= 0.0f) {
-                state = WRONG;
-                continue;
-            }
-            state = SURFACE;
-        }
-        if (F <= 0.0f) {
-            state = BEHIND;
-            continue;
-        }
-        float step = fmul(F, tmu);
-        if (step < ts) step = ts;
-        t = fadd(t, step);
-    }
-    if (!inside) return;
-    const size_t o = (size_t)v * in.W + u;
-    float4 V = make_float4(0.f, 0.f, 0.f, 0.f), N = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (state == BEHIND) {
-        for (int r = 0; r < 2; ++r) {
-#pragma unroll
-            for (int i = 0; i < 3; ++i) q[i] = fmul(fadd(org[i], fmul(t, dir[i])), inv_sv);
-            bool unused = true;
-            const float F = trilinear<MODE, false>(s, cache, q[0], q[1], q[2], unused);
-            t = fadd(t, fmul(F, tmu));
-        }
-        float p[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            p[i] = fadd(org[i], fmul(t, dir[i]));
-            q[i] = fmul(p[i], inv_sv);
-        }
-        if (coord_ok(q[0]) && coord_ok(q[1]) && coord_ok(q[2])) {
-            V = make_float4(p[0], p[1], p[2], 1.0f);
-            bool obs = true;
-            const float gx = fsub(trilinear<MODE, true>(s, cache, fadd(q[0], 1.0f), q[1], q[2], obs),
-                                  trilinear<MODE, true>(s, cache, fsub(q[0], 1.0f), q[1], q[2], obs));
-            const float gy = fsub(trilinear<MODE, true>(s, cache, q[0], fadd(q[1], 1.0f), q[2], obs),
-                                  trilinear<MODE, true>(s, cache, q[0], fsub(q[1], 1.0f), q[2], obs));
-            const float gz = fsub(trilinear<MODE, true>(s, cache, q[0], q[1], fadd(q[2], 1.0f), obs),
-                                  trilinear<MODE, true>(s, cache, q[0], q[1], fsub(q[2], 1.0f), obs));
-            const float gl = __fsqrt_rn(fadd(fadd(fmul(gx, gx), fmul(gy, gy)), fmul(gz, gz)));
-            if (obs && gl > 0.0f) N = make_float4(fdiv(gx, gl), fdiv(gy, gl), fdiv(gz, gl), 1.0f);
-        }
-    }
-    vtx[o] = V;
-    nrm[o] = N;
+    raycast_tile<MODE, RANGE>(s, in, T, vtx, nrm, max_iter, tB_m, inv_sv, rmin, rmax, tiles_x, tiles_y, blockIdx.x,
+                              blockIdx.y);
 }
 
 int range_grid()
