@@ -69,6 +69,48 @@ def render_frames(seed, indices, procs=None):
     return out
 
 
+def _render_small(args):
+    i, k = args
+    from synth import batched
+    w = batched.small_scenes()[i]
+    f = w.frame(k)
+    return i, k, f.depth, f.T_wc
+
+
+def render_batched_frames(n_steps, procs=None):
+    """Frames 0..n_steps-1 of the 64 small rooms, rendered by a spawn pool."""
+    jobs = [(i, k) for i in range(64) for k in range(n_steps)]
+    out = {}
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(procs or min(os.cpu_count() or 1, 32)) as pool:
+        for i, k, d, T in pool.imap_unordered(_render_small, jobs, chunksize=8):
+            out[(i, k)] = (d, T)
+    return out
+
+
+def _render_conf(args):
+    kind, a, b = args
+    if kind == "train":
+        from synth import confidence
+        w, f = confidence.training_frames()[a]
+        lab, _ = confidence.pixel_labels(f)
+        pix = confidence.sample_pixels(f, b, np.random.default_rng([11, a]))
+        return kind, a, f.depth, lab, pix
+    from synth import kinect_workload
+    f = kinect_workload(seed=7).frame(a)
+    return kind, a, f.depth, f.T_wc, None
+
+
+def render_learned_frames(n_train_samples=200_000, eval_frames=range(0, 60, 2)):
+    jobs = [("train", j, n_train_samples // 12) for j in range(12)] + [("eval", k, 0) for k in eval_frames]
+    out = {"train": {}, "eval": {}}
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(os.cpu_count() or 1, 32)) as pool:
+        for kind, a, d, x, y in pool.imap_unordered(_render_conf, jobs):
+            out[kind][a] = (d, x, y)
+    return out
+
+
 # ----------------------------------------------------------------- helpers
 
 def load_peaks():
@@ -257,6 +299,179 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+# ----------------------------------------------------------------- extra forms
+
+def run_batched_section(itm, torch, dev, frames_main, small_frames, n_steps, warmup):
+    """Pattern 2: per step one frame of each of 64 small rooms plus one frame
+    of the room sequence fused into its 1-3 active submaps, all in one batch
+    (persistent kernels replayed from a CUDA graph), after autotuning the
+    launch shapes."""
+    from paper_1708_00783_gb300 import autotune
+    from synth import batched
+    w_main, subs = batched.submaps()
+    small = batched.small_scenes()
+    sub_scenes = [itm.Scene(**p) for p, _ in subs]
+    small_scenes = [itm.Scene(**w.params) for w in small]
+    stream = torch.cuda.Stream(device=dev)
+    ci_main = itm.make_intrinsics(w_main.intr.width, w_main.intr.height, w_main.intr.fx, w_main.intr.fy,
+                                  w_main.intr.cx, w_main.intr.cy)
+    H, W = w_main.intr.height, w_main.intr.width
+    sub_out = [(torch.empty((H, W, 4), dtype=torch.float32, device=dev),
+                torch.empty((H, W, 4), dtype=torch.float32, device=dev)) for _ in subs]
+    small_ci = [itm.make_intrinsics(w.intr.width, w.intr.height, w.intr.fx, w.intr.fy, w.intr.cx, w.intr.cy)
+                for w in small]
+    small_out = [(torch.empty((w.intr.height, w.intr.width, 4), dtype=torch.float32, device=dev),
+                  torch.empty((w.intr.height, w.intr.width, 4), dtype=torch.float32, device=dev)) for w in small]
+    main_dev = {k: torch.from_numpy(itm_u16_to_float(frames_main[k][0])).to(dev) for k in range(n_steps)}
+    small_dev = {key: torch.from_numpy(np.ascontiguousarray(v[0])).to(dev) for key, v in small_frames.items()}
+    items_per_step = []
+    for k in range(n_steps):
+        items = []
+        T_world = frames_main[k][1].astype(np.float64)
+        for j in batched.active_submaps(k):
+            T = (np.linalg.inv(subs[j][1]) @ T_world).astype(np.float32)
+            items.append((sub_scenes[j].handle, main_dev[k], ci_main, T, sub_out[j][0], sub_out[j][1]))
+        for i in range(len(small)):
+            d, T = small_frames[(i, k)]
+            items.append((small_scenes[i].handle, small_dev[(i, k)], small_ci[i], T, small_out[i][0],
+                          small_out[i][1]))
+        items_per_step.append(itm.make_batch_items(items))
+    torch.cuda.synchronize()
+    batch = itm.itm_batch_create(max(len(x) for x in items_per_step))
+    counter = [0]
+
+    def step():
+        it = items_per_step[counter[0] % n_steps]
+        counter[0] += 1
+        itm.itm_batch_run(batch, it, stream=stream)
+
+    with torch.cuda.stream(stream):
+        tuned, tuned_ms, log, grids = autotune.tune_batch(batch, step, stream)
+        for _ in range(warmup):
+            step()
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+        torch.cuda.synchronize()
+        n_items = 0
+        for k in range(n_steps):
+            evs[k][0].record(stream)
+            itm.itm_batch_run(batch, items_per_step[k], stream=stream)
+            evs[k][1].record(stream)
+            n_items += len(items_per_step[k])
+            flush.zero_()
+        torch.cuda.synchronize()
+    ms = float(sum(a.elapsed_time(b) for a, b in evs))
+    bad = [sc.status() for sc in sub_scenes + small_scenes if sc.status() != 0]
+    itm.itm_batch_destroy(batch)
+    default_ms = log[0][2]
+    return {
+        "workload": "16 submaps of the room sequence (2^16..2^20 buckets, relative poses <= 15 deg / 0.5 m, 1-3 "
+                    "active per frame) + 64 rooms at 80x60..640x480 with 5-20 mm voxels; one frame per item",
+        "scene_frames_per_s": n_items / (ms / 1000.0),
+        "ms_per_step": ms / n_steps,
+        "items_per_step_mean": n_items / n_steps,
+        "steps": n_steps,
+        "launches_per_step": 8,
+        "cuda_graph": True,
+        "l2": "flushed between steps",
+        "autotune": {"ctas_per_sm": tuned, "grid_ctas": grids, "tuned_ms_per_step": tuned_ms,
+                     "default_ms_per_step": default_ms, "trials": len(log)},
+        "status_errors": bad,
+    }
+
+
+def itm_u16_to_float(raw):
+    """Host conversion used only to stage the batched section's inputs (the
+    timed per-frame path converts on the device)."""
+    return (raw.astype(np.float64) / 1000.0).astype(np.float32)
+
+
+def run_learned_section(itm, torch, dev, conf_frames):
+    """Pattern 4: train the confidence network with the library's kernels,
+    then fuse 30 frames of an unseen room with the learned weight; report its
+    per-frame throughput and the RMS TSDF error against the analytic SDF for
+    both weights (on 4000 sampled blocks observed by both)."""
+    from paper_1708_00783_gb300 import learned
+    from synth import kinect_workload
+    w = kinect_workload(seed=7)
+    ci = itm.make_intrinsics(w.intr.width, w.intr.height, w.intr.fx, w.intr.fy, w.intr.cx, w.intr.cy)
+    mu = w.params["mu"]
+    tr = conf_frames["train"]
+    depths = [tr[j][0] for j in sorted(tr)]
+    labels = [tr[j][1] for j in sorted(tr)]
+    pix = [tr[j][2] for j in sorted(tr)]
+    t0 = time.perf_counter()
+    feat, lab = learned.build_training_set(depths, ci, mu, pix, labels, device=dev)
+    model = learned.ConfidenceModel(device=dev, seed=0)
+    losses = model.train(feat, lab, steps=400, batch=8192, lr=3e-3)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    ev = conf_frames["eval"]
+    keys = sorted(ev)
+    H, W = w.intr.height, w.intr.width
+    dd = {k: torch.from_numpy(np.ascontiguousarray(ev[k][0])).to(dev) for k in keys}
+    wpx = torch.empty((H, W), dtype=torch.float32, device=dev)
+    vtx = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    nrm = torch.empty_like(vtx)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    sc_l = itm.Scene(**dict(w.params, weight_mode=1))
+    sc_c = itm.Scene(**w.params)
+    stage = []
+    for k in keys:
+        T = ev[k][1]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+        e[0].record(stream)
+        itm.itm_conf_weights(dd[k], ci, mu, model.packed, wpx, stream)
+        e[1].record(stream)
+        itm.itm_allocate(sc_l.handle, dd[k], ci, T, stream)
+        e[2].record(stream)
+        itm.itm_integrate_weighted(sc_l.handle, dd[k], wpx, ci, T, stream)
+        e[3].record(stream)
+        itm.itm_raycast(sc_l.handle, ci, T, vtx, nrm, stream)
+        e[4].record(stream)
+        stage.append(e)
+        flush.zero_()
+        itm.itm_process_frame(sc_c.handle, dd[k], ci, T, None, None, stream)
+        flush.zero_()
+    torch.cuda.synchronize()
+    st = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in stage])
+    ms = float(st.sum(axis=1).mean())
+    rms = _rms_pair(w, sc_c.export(), sc_l.export())
+    return {
+        "workload": "room seed 7, 640x480 @ 5 mm, 30 frames (0, 2, ..., 58) with noise and flying pixels",
+        "frames_per_s": 1000.0 / ms,
+        "stage_ms_mean": {"conf_weights": float(st[:, 0].mean()), "allocate": float(st[:, 1].mean()),
+                          "integrate_weighted": float(st[:, 2].mean()), "raycast": float(st[:, 3].mean())},
+        "conf_weights_mac_per_s": (w.intr.width * w.intr.height * (52 * 64 + 64 * 64 + 64)) /
+                                  (float(st[:, 0].mean()) / 1000.0),
+        "training": {"samples": int(lab.numel()), "steps": 400, "batch": 8192,
+                     "loss_first10": float(np.mean(losses[:10])), "loss_last10": float(np.mean(losses[-10:])),
+                     "seconds": train_s},
+        "rms_tsdf_error_m": rms,
+    }
+
+
+def _rms_pair(w, const, learned_):
+    coords_c, Fc, Wc = const
+    coords_l, Fl, Wl = learned_
+    oc, ol = np.lexsort(coords_c.T[::-1]), np.lexsort(coords_l.T[::-1])
+    coords_c, Fc, Wc = coords_c[oc], Fc[oc], Wc[oc]
+    Fl, Wl = Fl[ol], Wl[ol]
+    rng = np.random.default_rng(0)
+    sel = rng.choice(coords_c.shape[0], size=min(4000, coords_c.shape[0]), replace=False)
+    s = float(np.float32(w.params["voxel_size"]))
+    mu = w.params["mu"]
+    l = np.arange(512)
+    local = np.stack([l % 8, (l // 8) % 8, l // 64], axis=1)
+    g = coords_c[sel].astype(np.int64)[:, None, :] * 8 + local[None]
+    sdf = w.scene.sdf(g.reshape(-1, 3).astype(np.float64) * s).reshape(len(sel), 512)
+    m = (Wc[sel] > 0) & (Wl[sel] > 0) & (np.abs(sdf) < mu)
+    rc = float(np.sqrt(np.mean((Fc[sel][m] * mu - sdf[m]) ** 2)))
+    rl = float(np.sqrt(np.mean((Fl[sel][m] * mu - sdf[m]) ** 2)))
+    return {"constant": rc, "learned": rl, "voxels": int(m.sum()), "blocks_sampled": int(len(sel))}
+
+
 # ----------------------------------------------------------------- GPU arm
 
 def run_ours(args, world, rank, local):
@@ -266,6 +481,13 @@ def run_ours(args, world, rank, local):
     idx = sorted({k % N_FRAMES for k in range(total_frames)})
     frames = render_frames(seed, idx)
     cpu_frames = render_frames(0, list(range(0, N_FRAMES, 30))) if (rank == 0 and world == 1 and args.cpu_baseline) else None
+    extra = rank == 0 and world == 1
+    n_bsteps = 20
+    if extra and args.batched:
+        main_b = render_frames(0, list(range(n_bsteps)))
+        small_b = render_batched_frames(n_bsteps)
+    if extra and args.learned:
+        conf_frames = render_learned_frames()
 
     import torch
     torch.cuda.set_device(local)
@@ -377,6 +599,12 @@ def run_ours(args, world, rank, local):
         e2e = {"value": frames_all / (e_ms / 1000.0), "unit": "frames/s",
                "h2d_bytes_per_step": n_pix * 2, "d2h_bytes_per_step": 2 * n_pix * 16}
 
+    batched_rep = learned_rep = None
+    if extra and args.batched:
+        batched_rep = run_batched_section(itm, torch, dev, main_b, small_b, n_bsteps, warmup=3)
+    if extra and args.learned:
+        learned_rep = run_learned_section(itm, torch, dev, conf_frames)
+
     cpu = None
     if cpu_frames is not None:
         cpu = cpu_oracle_sample(cpu_frames)
@@ -428,6 +656,8 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": 8 * args.steps,  # u16, enumerate, commit, overflow, visible, integrate, range, raycast
+        "batched": batched_rep,
+        "learned": learned_rep,
     }
     print(json.dumps(line), flush=True)
 
@@ -440,6 +670,8 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--no-learned", dest="learned", action="store_false")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -475,17 +475,23 @@ def tiny_workload(seed: int = 0, n_frames: int = 10, noise_scale: float = 1.0) -
                     n_frames, scene, pose, seed, 0.0, (0.0, 5.0), noise_scale)
 
 
-def kinect_workload(seed: int = 0, n_frames: int = 300) -> Workload:
-    """640x480 Kinect-like sequence in a 4x3x2.5 m room with 20 primitives."""
-    intr = Intrinsics(640, 480, 525.0, 525.0, 319.5, 239.5)
+def kinect_workload(seed: int = 0, n_frames: int = 300, width: int = 640, height: int = 480,
+                    params: Optional[dict] = None) -> Workload:
+    """640x480 Kinect-like sequence in a 4x3x2.5 m room with 20 primitives
+    (other image sizes keep the field of view: focal length scaled with the
+    width)."""
+    sc = width / 640.0
+    intr = Intrinsics(width, height, 525.0 * sc, 525.0 * sc, (width - 1) / 2.0, (height - 1) / 2.0)
     rng = np.random.default_rng([seed, 1])
     lo, hi = (-2.0, 0.0, -1.5), (2.0, 2.5, 1.5)
     prims: List[Primitive] = [RoomInside(lo, hi)] + _room_primitives(rng, lo, hi, 20)
     pose = _smooth_path(np.random.default_rng([seed, 2]), n_frames, 30.0,
                         (-1.5, 0.5, -1.0), (1.5, 2.0, 1.0), 0.5, 30.0,
                         yaw0=rng.uniform(0, 2 * np.pi), yaw_amp=2.0, pitch_amp=0.3)
-    return Workload("kinect", intr, _params(0.005, 0.02, 100, 1 << 20, 1 << 17, 1 << 19, 0.4, 5.0),
-                    n_frames, AnalyticScene(prims), pose, seed, 0.01, (0.4, 5.0))
+    p = _params(0.005, 0.02, 100, 1 << 20, 1 << 17, 1 << 19, 0.4, 5.0)
+    if params:
+        p.update(params)
+    return Workload("kinect", intr, p, n_frames, AnalyticScene(prims), pose, seed, 0.01, (0.4, 5.0))
 
 
 def large_workload(seed: int = 0, n_frames: int = 1000, num_buckets: int = 1 << 22) -> Workload:
