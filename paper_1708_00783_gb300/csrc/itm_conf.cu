@@ -73,13 +73,14 @@ __device__ __forceinline__ bool conf_features(const Depth &D, const Intr &in, fl
 #pragma unroll
     for (int k = 0; k < NF; ++k) x[k] = 0.0f;
     if (!(dc > 0.0f)) return false;
+    const float inv_mu = 1.0f / mu;
 #pragma unroll
     for (int i = -3; i <= 3; ++i)
 #pragma unroll
         for (int j = -3; j <= 3; ++j) {
             const float d = D(u + j, v + i);
             float f = 0.0f;
-            if (d > 0.0f) f = fminf(fmaxf((d - dc) / mu, -4.0f), 4.0f);
+            if (d > 0.0f) f = fminf(fmaxf((d - dc) * inv_mu, -4.0f), 4.0f);
             x[(i + 3) * 7 + (j + 3)] = f;
         }
     const float dl = D(u - 1, v), dr = D(u + 1, v), du = D(u, v - 1), dd = D(u, v + 1);

@@ -44,7 +44,7 @@ struct Counters {
     int32_t n_overflow;     // per-frame: requests that lost their bucket
     int32_t n_visible;      // per-frame: visible blocks
     int32_t depth_max_bits; // per-frame: largest valid depth (float bits, >= 0)
-    int32_t pad0;
+    int32_t ray_next;       // per-raycast: next 8x4 tile handed to a warp
     unsigned long long updated;  // cumulative voxel updates
     unsigned long long visited;  // cumulative voxels visited by integration
     unsigned long long frames;   // cumulative integrated frames
@@ -53,6 +53,7 @@ struct Counters {
 // Offset and size of the per-frame counters cleared at the start of allocation.
 constexpr size_t kFrameCountersOffset = 12;  // n_req
 constexpr size_t kFrameCountersBytes = 16;   // n_req .. depth_max_bits
+constexpr size_t kRayNextOffset = 28;        // ray_next
 
 struct SceneDev {
     Entry *entries;

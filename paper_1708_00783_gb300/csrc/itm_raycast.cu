@@ -64,6 +64,27 @@ __global__ void __launch_bounds__(256) range_kernel(SceneDev s, Mat34 M, Intr in
     }
 }
 
+// Persistent raycast: each warp takes the next 8x4 tile from a device counter
+// until none is left, so warps that finish early pick up more work instead of
+// idling behind the slowest tiles of a fixed grid.
+template <int MODE>
+__global__ void __launch_bounds__(256) raycast_dynamic_kernel(SceneDev s, Intr in, Mat34 T, float4 *__restrict__ vtx,
+                                                              float4 *__restrict__ nrm, int max_iter, float tB_m,
+                                                              float inv_sv, const uint32_t *__restrict__ rmin,
+                                                              const uint32_t *__restrict__ rmax, int tiles_x,
+                                                              int n_tiles)
+{
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&s.ctr->ray_next, 1);
+        t = __shfl_sync(kFull, t, 0);
+        if (t >= n_tiles) return;
+        raycast_warp_tile<MODE, true>(s, in, T, vtx, nrm, max_iter, tB_m, inv_sv, rmin, rmax, tiles_x, t % tiles_x,
+                                      t / tiles_x);
+    }
+}
+
 template <int MODE, bool RANGE>
 __global__ void __launch_bounds__(256) raycast_kernel(SceneDev s, Intr in, Mat34 T, float4 *__restrict__ vtx,
                                                       float4 *__restrict__ nrm, int max_iter, float tB_m,
@@ -116,13 +137,27 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
     const int tx = (in.W + 7) / 8, ty = (in.H + 3) / 4;
     if (range_fits(in)) {
         cudaError_t e = launch_raycast_range(s, in, M_d, s.range_min, s.range_max, st);
+        if (e == cudaSuccess)
+            e = cudaMemsetAsync(reinterpret_cast<char *>(s.ctr) + kRayNextOffset, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return e;
-        if (s.weight_mode == 0)
-            raycast_kernel<0, true><<<grid, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
-                                                          s.range_max, tx, ty);
+        static int g_dyn[2] = {0, 0};
+        const int mode = s.weight_mode ? 1 : 0;
+        if (!g_dyn[mode]) {
+            int dev = 0, sms = 1, per = 1;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per, mode ? (const void *)raycast_dynamic_kernel<1> : (const void *)raycast_dynamic_kernel<0>, 256, 0);
+            g_dyn[mode] = sms * (per > 0 ? per : 1);
+        }
+        const int n_tiles = tx * ty;
+        const int g = g_dyn[mode] < (n_tiles + 7) / 8 ? g_dyn[mode] : (n_tiles + 7) / 8;
+        if (mode == 0)
+            raycast_dynamic_kernel<0><<<g, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
+                                                         s.range_max, tx, n_tiles);
         else
-            raycast_kernel<1, true><<<grid, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
-                                                          s.range_max, tx, ty);
+            raycast_dynamic_kernel<1><<<g, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
+                                                         s.range_max, tx, n_tiles);
     } else {
         if (s.weight_mode == 0)
             raycast_kernel<0, false><<<grid, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, nullptr,
