@@ -64,6 +64,20 @@ __global__ void __launch_bounds__(256) build_visible_kernel(SceneDev s, Mat34 M,
     }
 }
 
+// The same, also filling the search range of a raycast from this pose (the
+// loop is uniform per CTA so every warp reaches the rasterisation together).
+__global__ void __launch_bounds__(256) build_visible_range_kernel(SceneDev s, Mat34 M, Intr in, float zc,
+                                                                  int tiles_x, int tiles_y)
+{
+    const int n = min(__ldcg(&s.ctr->block_head), s.nv);
+    const float zfar = visible_zfar(s);
+    const int stride = gridDim.x * blockDim.x;
+    for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
+        const int i = i0 + threadIdx.x;
+        visible_and_range(s, M, in, zfar, i < n, i, zc, tiles_x, tiles_y);
+    }
+}
+
 int persistent_grid(int threads, const void *kernel)
 {
     static int cached_sm = 0;
@@ -82,7 +96,7 @@ int persistent_grid(int threads, const void *kernel)
 }  // namespace
 
 cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &in, const Mat34 &T_wc,
-                            const Mat34 &M_d, cudaStream_t st)
+                            const Mat34 &M_d, bool with_range, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(reinterpret_cast<char *>(s.ctr) + kFrameCountersOffset, 0,
                                     kFrameCountersBytes, st);
@@ -90,12 +104,21 @@ cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &i
     const float inv_b = (float)(1.0 / (8.0 * (double)s.voxel_size));
     dim3 grid((in.W + 31) / 32, (in.H + 7) / 8);
     alloc_enumerate_kernel<<<grid, 256, 0, st>>>(s, depth, in, T_wc, inv_b);
-    static int g_commit = 0, g_visible = 0;
+    static int g_commit = 0, g_visible = 0, g_visrange = 0;
     if (!g_commit) g_commit = persistent_grid(256, (const void *)alloc_commit_kernel);
     if (!g_visible) g_visible = persistent_grid(256, (const void *)build_visible_kernel);
+    if (!g_visrange) g_visrange = persistent_grid(256, (const void *)build_visible_range_kernel);
     alloc_commit_kernel<<<g_commit, 256, 0, st>>>(s);
     alloc_overflow_kernel<<<1, kOvfThreads, 0, st>>>(s);
-    build_visible_kernel<<<g_visible, 256, 0, st>>>(s, M_d, in);
+    if (with_range) {
+        const int tx = (in.W + 7) / 8, ty = (in.H + 3) / 4;
+        e = cudaMemsetAsync(s.range_min, 0xff, sizeof(uint32_t) * (size_t)tx * ty, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(s.range_max, 0, sizeof(uint32_t) * (size_t)tx * ty, st);
+        if (e != cudaSuccess) return e;
+        build_visible_range_kernel<<<g_visrange, 256, 0, st>>>(s, M_d, in, s.z_min - 1e-3f, tx, ty);
+    } else {
+        build_visible_kernel<<<g_visible, 256, 0, st>>>(s, M_d, in);
+    }
     return cudaGetLastError();
 }
 

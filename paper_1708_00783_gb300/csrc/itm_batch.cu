@@ -442,7 +442,10 @@ int itm_batch_run(itm_batch *b, const itm_batch_item *items, int n, itm_stream s
     } else {
         e = launch_stages(b, st);
     }
-    for (int i = 0; i < n; ++i) items[i].scene->last_stream = st;
+    for (int i = 0; i < n; ++i) {
+        items[i].scene->last_stream = st;
+        items[i].scene->alloc_epoch++;  // the batch rewrote the scene's range tiles
+    }
     return check_cuda(e);
 }
 

@@ -187,6 +187,12 @@ struct itm_scene {
     itm::SceneDev d;
     cudaStream_t last_stream;
     int device;
+    // the search-range tiles hold the range of a raycast from range_pose /
+    // range_intr over the blocks allocated at epoch range_epoch
+    long long alloc_epoch;
+    long long range_epoch;
+    float range_pose[16];
+    itm_intrinsics range_intr;
 };
 
 // Host helpers implemented in itm_scene.cu.
@@ -201,11 +207,11 @@ Intr to_intr(const itm_intrinsics *in);
 // Launchers implemented in the kernel translation units.
 namespace itm {
 cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &in, const Mat34 &T_wc,
-                            const Mat34 &M_d, cudaStream_t st);
+                            const Mat34 &M_d, bool with_range, cudaStream_t st);
 cudaError_t launch_integrate(const SceneDev &s, const float *depth, const float *wpx, const Intr &in,
                              const Mat34 &M_d, cudaStream_t st);
 cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, const Mat34 &M_d, float4 *vtx,
-                           float4 *nrm, cudaStream_t st);
+                           float4 *nrm, bool range_ready, cudaStream_t st);
 cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 &M_d, uint32_t *rmin, uint32_t *rmax,
                                  cudaStream_t st);
 bool range_fits(const Intr &in);

@@ -124,7 +124,7 @@ cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 
 }
 
 cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, const Mat34 &M_d, float4 *vtx,
-                           float4 *nrm, cudaStream_t st)
+                           float4 *nrm, bool range_ready, cudaStream_t st)
 {
     // host-side constants with the same float operations as the oracle
     volatile float span = s.z_max - s.z_min;
@@ -136,7 +136,8 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
     dim3 grid((in.W + 31) / 32, (in.H + 7) / 8);
     const int tx = (in.W + 7) / 8, ty = (in.H + 3) / 4;
     if (range_fits(in)) {
-        cudaError_t e = launch_raycast_range(s, in, M_d, s.range_min, s.range_max, st);
+        // the allocation of this frame may have filled the range already
+        cudaError_t e = range_ready ? cudaSuccess : launch_raycast_range(s, in, M_d, s.range_min, s.range_max, st);
         if (e == cudaSuccess)
             e = cudaMemsetAsync(reinterpret_cast<char *>(s.ctr) + kRayNextOffset, 0, sizeof(int32_t), st);
         if (e != cudaSuccess) return e;

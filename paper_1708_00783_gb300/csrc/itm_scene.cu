@@ -169,6 +169,7 @@ int itm_scene_destroy(itm_scene *sc)
 int itm_scene_reset(itm_scene *sc, itm_stream stream)
 {
     if (!sc) return ITM_ERR_ARG;
+    sc->alloc_epoch++;
     cudaStream_t st = (cudaStream_t)stream;
     sc->last_stream = st;
     return check_cuda(launch_reset(sc->d, st));
@@ -183,7 +184,17 @@ int itm_allocate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *in
     rigid_inverse_rows(T_wc, M);
     cudaStream_t st = (cudaStream_t)stream;
     sc->last_stream = st;
-    return check_cuda(launch_allocate(sc->d, depth_dev, to_intr(intr), T, M, st));
+    const Intr in = to_intr(intr);
+    const bool with_range = range_fits(in);
+    sc->alloc_epoch++;
+    const int r = check_cuda(launch_allocate(sc->d, depth_dev, in, T, M, with_range, st));
+    if (r == ITM_OK && with_range) {
+        // the range tiles now hold the range of a raycast from this pose
+        sc->range_epoch = sc->alloc_epoch;
+        memcpy(sc->range_pose, T_wc, sizeof(sc->range_pose));
+        sc->range_intr = *intr;
+    }
+    return r;
 }
 
 int itm_integrate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
@@ -221,14 +232,24 @@ int itm_raycast(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16],
     rigid_inverse_rows(T_wc, M);
     cudaStream_t st = (cudaStream_t)stream;
     sc->last_stream = st;
-    return check_cuda(launch_raycast(sc->d, to_intr(intr), T, M, reinterpret_cast<float4 *>(vertex_dev),
-                                     reinterpret_cast<float4 *>(normal_dev), st));
+    const bool ready = sc->range_epoch == sc->alloc_epoch && memcmp(sc->range_pose, T_wc, sizeof(sc->range_pose)) == 0 &&
+                       memcmp(&sc->range_intr, intr, sizeof(itm_intrinsics)) == 0;
+    const int r = check_cuda(launch_raycast(sc->d, to_intr(intr), T, M, reinterpret_cast<float4 *>(vertex_dev),
+                                            reinterpret_cast<float4 *>(normal_dev), ready, st));
+    if (r == ITM_OK && range_fits(to_intr(intr))) {
+        sc->range_epoch = sc->alloc_epoch;
+        memcpy(sc->range_pose, T_wc, sizeof(sc->range_pose));
+        sc->range_intr = *intr;
+    }
+    return r;
 }
 
 int itm_raycast_range(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16], float *zmin_dev,
                       float *zmax_dev, itm_stream stream)
 {
     if (!sc || !valid_pose(T_wc) || !zmin_dev || !zmax_dev || !valid_intr(intr)) return ITM_ERR_ARG;
+    if (zmin_dev == reinterpret_cast<float *>(sc->d.range_min) || zmax_dev == reinterpret_cast<float *>(sc->d.range_max))
+        return ITM_ERR_ARG;
     Mat34 M;
     rigid_inverse_rows(T_wc, M);
     cudaStream_t st = (cudaStream_t)stream;
@@ -415,6 +436,7 @@ int itm_scene_import(itm_scene *sc, const int16_t *coords_host, const float *sdf
             w8[i] = (uint8_t)w;
         }
     }
+    sc->alloc_epoch++;
     cudaError_t e = cudaStreamSynchronize(sc->last_stream);
     if (e == cudaSuccess) e = launch_reset(d, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
