@@ -212,6 +212,11 @@ def max_over_ranks(value, world, device=None):
     return float(t.item())
 
 
+def job_throughput(units_per_rank, world, max_ms):
+    """Units processed by all ranks divided by the slowest rank's time (s)."""
+    return units_per_rank * world / (max_ms / 1000.0)
+
+
 def sum_over_ranks(value, world, device=None):
     if world <= 1:
         return value
@@ -552,7 +557,7 @@ def run_ours(args, world, rank, local):
     total_ms = float(step_ms.sum())
     total_ms_max = max_over_ranks(total_ms, world, dev)
     frames_all = args.steps * world
-    fps = frames_all / (total_ms_max / 1000.0)
+    fps = job_throughput(args.steps, world, total_ms_max)
     updated = st1["updated_voxels"] - st0["updated_voxels"]
     visited = st1["visited_voxels"] - st0["visited_voxels"]
     updated_all = sum_over_ranks(float(updated), world, dev)
