@@ -122,8 +122,8 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
-    p = os.path.join(ROOT, "paper_1708_00783_gb300", "csrc", "itm_integrate.cu")
+def kernel_source_hash(name="itm_integrate.cu"):
+    p = os.path.join(ROOT, "paper_1708_00783_gb300", "csrc", name)
     with open(p, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
@@ -136,7 +136,7 @@ def committed_traffic():
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("source_sha256_16") != kernel_source_hash():
+    if d.get("source_sha256_16") != kernel_source_hash() or d.get("ops_sha256_16") != kernel_source_hash("itm_ops.cuh"):
         return None
     return d.get("dram_bytes_per_launch_scaled")
 
