@@ -660,7 +660,7 @@ def run_ours(args, world, rank, local):
         "cpu_baseline": cpu,
         "clocks": clocks,
         "e2e": e2e,
-        "gpu_launches": 8 * args.steps,  # u16, enumerate, commit, overflow, visible, integrate, range, raycast
+        "gpu_launches": 6 * args.steps,  # u16, enumerate, commit (+ overflow), visible + range, integrate, raycast
         "batched": batched_rep,
         "learned": learned_rep,
     }

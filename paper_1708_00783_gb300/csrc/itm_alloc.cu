@@ -1,4 +1,4 @@
-// Sec. 4.2 allocation on the GPU, in four launches per frame:
+// Sec. 4.2 allocation on the GPU, in three launches per frame:
 //
 //  1. alloc_enumerate  one thread per pixel walks the blocks crossed by its
 //     segment d-mu .. d+mu (3D DDA).  The 32 lanes of a warp cover an 8x4
@@ -13,14 +13,16 @@
 //     (Sec. 3.3 insertion).  Each bucket's chain has exactly one writer, so
 //     chains are extended without locks; blocks and excess slots come from
 //     prepopulated free lists through warp-aggregated atomic counters (the
-//     paper's "atomic subtraction on a stack").
-//  3. alloc_overflow   one CTA resolves the overflow list in rounds: look up,
-//     claim the bucket, let winners insert, repeat with the losers.  The
-//     paper leaves such intra-frame collisions for the next frame; resolving
-//     them makes the allocated set the complete union over all pixels.
-//  4. build_visible    every allocated block whose voxels can project into the
+//     paper's "atomic subtraction on a stack").  The CTA that finishes last
+//     then resolves the overflow list in rounds: look up, claim the bucket,
+//     let winners insert, repeat with the losers.  The paper leaves such
+//     intra-frame collisions for the next frame; resolving them makes the
+//     allocated set the complete union over all pixels.
+//  3. build_visible    every allocated block whose voxels can project into the
 //     image with z > 0 and lie within the frame's depth range + mu is
-//     appended to the visible list (Sec. 4.2, third part).
+//     appended to the visible list (Sec. 4.2, third part); eight lanes per
+//     block, one per corner.  When the raycast will use the allocation pose,
+//     the same pass also rasterises each block's search range.
 //
 // Counts produced on the device are read by the next kernel from device
 // memory (persistent grid-stride loops), so no host synchronisation and no
@@ -31,36 +33,48 @@ namespace itm {
 
 namespace {
 
+// Also clears the search-range tiles of this frame (n_range_tiles of them;
+// nothing reads them before the visible-list pass).
 __global__ void __launch_bounds__(256) alloc_enumerate_kernel(SceneDev s, const float *__restrict__ depth,
-                                                              Intr in, Mat34 T, float inv_b)
+                                                              Intr in, Mat34 T, float inv_b, int n_range_tiles)
 {
+    const int cta = blockIdx.y * gridDim.x + blockIdx.x, ctas = gridDim.x * gridDim.y;
+    for (int i = cta * blockDim.x + threadIdx.x; i < n_range_tiles; i += ctas * blockDim.x) {
+        s.range_min[i] = 0xffffffffu;
+        s.range_max[i] = 0u;
+    }
     enumerate_tile(s, depth, in, T, inv_b, blockIdx.x, blockIdx.y);
 }
 
+// The last CTA to finish its requests then resolves the overflow list (its
+// inserts are visible through the fences before the completion count).
 __global__ void __launch_bounds__(256) alloc_commit_kernel(SceneDev s)
 {
+    __shared__ int is_last, remaining;
     const int n = min(__ldcg(&s.ctr->n_req), s.nb);
     const int stride = gridDim.x * blockDim.x;
     for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
         const int i = i0 + threadIdx.x;
         if (i < n) commit_request(s, i);
     }
-}
-
-__global__ void __launch_bounds__(kOvfThreads) alloc_overflow_kernel(SceneDev s)
-{
-    __shared__ int remaining;
-    overflow_scene(s, remaining);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&s.ctr->commit_done, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (is_last) {
+        __threadfence();
+        overflow_scene(s, remaining);
+    }
 }
 
 __global__ void __launch_bounds__(256) build_visible_kernel(SceneDev s, Mat34 M, Intr in)
 {
     const int n = min(__ldcg(&s.ctr->block_head), s.nv);
     const float zfar = visible_zfar(s);
-    const int stride = gridDim.x * blockDim.x;
-    for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
-        const int i = i0 + threadIdx.x;
-        if (i < n) visible_block(s, M, in, zfar, i);
+    const int groups = gridDim.x * (blockDim.x >> 3);
+    for (int g0 = blockIdx.x * (blockDim.x >> 3); g0 < n; g0 += groups) {
+        const int i = g0 + (threadIdx.x >> 3);
+        visible_8<false>(s, M, in, zfar, i < n, i, 0.0f, 1, 1);
     }
 }
 
@@ -71,10 +85,10 @@ __global__ void __launch_bounds__(256) build_visible_range_kernel(SceneDev s, Ma
 {
     const int n = min(__ldcg(&s.ctr->block_head), s.nv);
     const float zfar = visible_zfar(s);
-    const int stride = gridDim.x * blockDim.x;
-    for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
-        const int i = i0 + threadIdx.x;
-        visible_and_range(s, M, in, zfar, i < n, i, zc, tiles_x, tiles_y);
+    const int groups = gridDim.x * (blockDim.x >> 3);
+    for (int g0 = blockIdx.x * (blockDim.x >> 3); g0 < n; g0 += groups) {
+        const int i = g0 + (threadIdx.x >> 3);
+        visible_8<true>(s, M, in, zfar, i < n, i, zc, tiles_x, tiles_y);
     }
 }
 
@@ -103,18 +117,15 @@ cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &i
     if (e != cudaSuccess) return e;
     const float inv_b = (float)(1.0 / (8.0 * (double)s.voxel_size));
     dim3 grid((in.W + 31) / 32, (in.H + 7) / 8);
-    alloc_enumerate_kernel<<<grid, 256, 0, st>>>(s, depth, in, T_wc, inv_b);
+    const int n_range_tiles = with_range ? ((in.W + 7) / 8) * ((in.H + 3) / 4) : 0;
+    alloc_enumerate_kernel<<<grid, 256, 0, st>>>(s, depth, in, T_wc, inv_b, n_range_tiles);
     static int g_commit = 0, g_visible = 0, g_visrange = 0;
     if (!g_commit) g_commit = persistent_grid(256, (const void *)alloc_commit_kernel);
     if (!g_visible) g_visible = persistent_grid(256, (const void *)build_visible_kernel);
     if (!g_visrange) g_visrange = persistent_grid(256, (const void *)build_visible_range_kernel);
     alloc_commit_kernel<<<g_commit, 256, 0, st>>>(s);
-    alloc_overflow_kernel<<<1, kOvfThreads, 0, st>>>(s);
     if (with_range) {
         const int tx = (in.W + 7) / 8, ty = (in.H + 3) / 4;
-        e = cudaMemsetAsync(s.range_min, 0xff, sizeof(uint32_t) * (size_t)tx * ty, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(s.range_max, 0, sizeof(uint32_t) * (size_t)tx * ty, st);
-        if (e != cudaSuccess) return e;
         build_visible_range_kernel<<<g_visrange, 256, 0, st>>>(s, M_d, in, s.z_min - 1e-3f, tx, ty);
     } else {
         build_visible_kernel<<<g_visible, 256, 0, st>>>(s, M_d, in);

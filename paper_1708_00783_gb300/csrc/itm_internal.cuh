@@ -44,7 +44,9 @@ struct Counters {
     int32_t n_overflow;     // per-frame: requests that lost their bucket
     int32_t n_visible;      // per-frame: visible blocks
     int32_t depth_max_bits; // per-frame: largest valid depth (float bits, >= 0)
+    int32_t commit_done;    // per-frame: CTAs of the commit kernel that finished
     int32_t ray_next;       // per-raycast: next 8x4 tile handed to a warp
+    int32_t pad0;
     unsigned long long updated;  // cumulative voxel updates
     unsigned long long visited;  // cumulative voxels visited by integration
     unsigned long long frames;   // cumulative integrated frames
@@ -52,8 +54,8 @@ struct Counters {
 
 // Offset and size of the per-frame counters cleared at the start of allocation.
 constexpr size_t kFrameCountersOffset = 12;  // n_req
-constexpr size_t kFrameCountersBytes = 16;   // n_req .. depth_max_bits
-constexpr size_t kRayNextOffset = 28;        // ray_next
+constexpr size_t kFrameCountersBytes = 20;   // n_req .. commit_done
+constexpr size_t kRayNextOffset = 32;        // ray_next
 
 struct SceneDev {
     Entry *entries;
