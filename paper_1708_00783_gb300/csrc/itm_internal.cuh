@@ -25,6 +25,8 @@ constexpr int kBlockVoxels = 512;
 // largest image whose raycast uses the search-range tiles (8x4 pixels each)
 constexpr int kRangeMaxW = 4096, kRangeMaxH = 4096;
 constexpr int kRangeMaxTiles = (kRangeMaxW / 8) * (kRangeMaxH / 4);
+// largest tile count whose hand-out order is re-sorted at the end of a raycast
+constexpr int kOrderMaxTiles = 1 << 16;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Sec. 3.2 hash entry.  Bytes 0..7 (x, y, z, flag) form the packed block key
@@ -46,7 +48,7 @@ struct Counters {
     int32_t depth_max_bits; // per-frame: largest valid depth (float bits, >= 0)
     int32_t commit_done;    // per-frame: CTAs of the commit kernel that finished
     int32_t ray_next;       // per-raycast: next 8x4 tile handed to a warp
-    int32_t pad0;
+    int32_t ray_done;       // per-raycast: CTAs of the raycast kernel that finished
     unsigned long long updated;  // cumulative voxel updates
     unsigned long long visited;  // cumulative voxels visited by integration
     unsigned long long frames;   // cumulative integrated frames
@@ -55,7 +57,8 @@ struct Counters {
 // Offset and size of the per-frame counters cleared at the start of allocation.
 constexpr size_t kFrameCountersOffset = 12;  // n_req
 constexpr size_t kFrameCountersBytes = 20;   // n_req .. commit_done
-constexpr size_t kRayNextOffset = 32;        // ray_next
+constexpr size_t kRayNextOffset = 32;        // ray_next, ray_done
+constexpr size_t kRayNextBytes = 8;
 
 struct SceneDev {
     Entry *entries;
@@ -72,6 +75,8 @@ struct SceneDev {
     Counters *ctr;
     uint32_t *range_min;  // per 8x4 tile: nearest / farthest depth (float bits) of covering blocks
     uint32_t *range_max;
+    uint8_t *tile_cost;   // per 8x4 tile: march iterations of the last raycast (+8 with a hit), <= 255
+    int32_t *tile_order;  // tiles ordered by decreasing tile_cost: hand-out order of the next raycast
     int nb, ne, nv;
     int ovf_cap;
     float voxel_size, mu, z_min, z_max;
@@ -195,6 +200,9 @@ struct itm_scene {
     long long range_epoch;
     float range_pose[16];
     itm_intrinsics range_intr;
+    // tile_order is a permutation of the tiles of a tiles_x x tiles_y image
+    // ({0, 0}: none yet)
+    int order_dims[2];
 };
 
 // Host helpers implemented in itm_scene.cu.
@@ -213,7 +221,7 @@ cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &i
 cudaError_t launch_integrate(const SceneDev &s, const float *depth, const float *wpx, const Intr &in,
                              const Mat34 &M_d, cudaStream_t st);
 cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, const Mat34 &M_d, float4 *vtx,
-                           float4 *nrm, bool range_ready, cudaStream_t st);
+                           float4 *nrm, bool range_ready, int order_dims[2], cudaStream_t st);
 cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 &M_d, uint32_t *rmin, uint32_t *rmax,
                                  cudaStream_t st);
 bool range_fits(const Intr &in);

@@ -64,25 +64,73 @@ __global__ void __launch_bounds__(256) range_kernel(SceneDev s, Mat34 M, Intr in
     }
 }
 
+// Hand-out order of the next raycast: the n tiles by decreasing cost (a
+// counting sort over the 256 cost values, one CTA of 256 threads; the order
+// within one cost value is that of the atomics).
+__device__ void order_tiles_by_cost(const SceneDev &s, int n)
+{
+    __shared__ int bin[256];
+    __shared__ int warp_sum[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    bin[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += 256) atomicAdd(&bin[255 - (int)__ldcg(&s.tile_cost[i])], 1);
+    __syncthreads();
+    // exclusive scan of the bins, bin 0 (cost 255) first
+    const int c = bin[tid];
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sum[warp] = x;
+    __syncthreads();
+    int base = 0;
+    for (int w = 0; w < warp; ++w) base += warp_sum[w];
+    bin[tid] = base + x - c;
+    __syncthreads();
+    for (int i = tid; i < n; i += 256) {
+        const int p = atomicAdd(&bin[255 - (int)__ldcg(&s.tile_cost[i])], 1);
+        s.tile_order[p] = i;
+    }
+}
+
 // Persistent raycast: each warp takes the next 8x4 tile from a device counter
 // until none is left, so warps that finish early pick up more work instead of
-// idling behind the slowest tiles of a fixed grid.
+// idling behind the slowest tiles of a fixed grid.  With use_order the tiles
+// are handed out in tile_order (longest-processing-time first, by the costs
+// of the previous raycast), so the expensive tiles do not start last.  With
+// write_order every tile's cost is recorded and the CTA that finishes last
+// sorts them into tile_order for the next raycast.
 template <int MODE>
 __global__ void __launch_bounds__(256) raycast_dynamic_kernel(SceneDev s, Intr in, Mat34 T, float4 *__restrict__ vtx,
                                                               float4 *__restrict__ nrm, int max_iter, float tB_m,
                                                               float inv_sv, const uint32_t *__restrict__ rmin,
                                                               const uint32_t *__restrict__ rmax, int tiles_x,
-                                                              int n_tiles)
+                                                              int n_tiles, bool use_order, bool write_order)
 {
+    __shared__ int is_last;
     const int lane = threadIdx.x & 31;
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(&s.ctr->ray_next, 1);
         t = __shfl_sync(kFull, t, 0);
-        if (t >= n_tiles) return;
-        raycast_warp_tile<MODE, true>(s, in, T, vtx, nrm, max_iter, tB_m, inv_sv, rmin, rmax, tiles_x, t % tiles_x,
-                                      t / tiles_x);
+        if (t >= n_tiles) break;
+        // tile_order is rewritten only after every CTA has left this loop
+        const int tile = use_order ? __ldcg(&s.tile_order[t]) : t;
+        const int cost = raycast_warp_tile<MODE, true>(s, in, T, vtx, nrm, max_iter, tB_m, inv_sv, rmin, rmax,
+                                                       tiles_x, tile % tiles_x, tile / tiles_x);
+        if (write_order && lane == 0) s.tile_cost[tile] = (uint8_t)cost;
     }
+    if (!write_order) return;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&s.ctr->ray_done, 1) == (int)gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    order_tiles_by_cost(s, n_tiles);
 }
 
 template <int MODE, bool RANGE>
@@ -124,7 +172,7 @@ cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 
 }
 
 cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, const Mat34 &M_d, float4 *vtx,
-                           float4 *nrm, bool range_ready, cudaStream_t st)
+                           float4 *nrm, bool range_ready, int order_dims[2], cudaStream_t st)
 {
     // host-side constants with the same float operations as the oracle
     volatile float span = s.z_max - s.z_min;
@@ -139,7 +187,7 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
         // the allocation of this frame may have filled the range already
         cudaError_t e = range_ready ? cudaSuccess : launch_raycast_range(s, in, M_d, s.range_min, s.range_max, st);
         if (e == cudaSuccess)
-            e = cudaMemsetAsync(reinterpret_cast<char *>(s.ctr) + kRayNextOffset, 0, sizeof(int32_t), st);
+            e = cudaMemsetAsync(reinterpret_cast<char *>(s.ctr) + kRayNextOffset, 0, kRayNextBytes, st);
         if (e != cudaSuccess) return e;
         static int g_dyn[2] = {0, 0};
         const int mode = s.weight_mode ? 1 : 0;
@@ -153,12 +201,21 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
         }
         const int n_tiles = tx * ty;
         const int g = g_dyn[mode] < (n_tiles + 7) / 8 ? g_dyn[mode] : (n_tiles + 7) / 8;
+        const bool write_order = n_tiles <= kOrderMaxTiles;
+        const bool use_order = write_order && order_dims[0] == tx && order_dims[1] == ty;
         if (mode == 0)
             raycast_dynamic_kernel<0><<<g, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
-                                                         s.range_max, tx, n_tiles);
+                                                         s.range_max, tx, n_tiles, use_order, write_order);
         else
             raycast_dynamic_kernel<1><<<g, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
-                                                         s.range_max, tx, n_tiles);
+                                                         s.range_max, tx, n_tiles, use_order, write_order);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        if (write_order) {
+            order_dims[0] = tx;
+            order_dims[1] = ty;
+        }
+        return cudaSuccess;
     } else {
         if (s.weight_mode == 0)
             raycast_kernel<0, false><<<grid, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, nullptr,
