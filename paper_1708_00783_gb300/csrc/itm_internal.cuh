@@ -25,8 +25,12 @@ constexpr int kBlockVoxels = 512;
 // largest image whose raycast uses the search-range tiles (8x4 pixels each)
 constexpr int kRangeMaxW = 4096, kRangeMaxH = 4096;
 constexpr int kRangeMaxTiles = (kRangeMaxW / 8) * (kRangeMaxH / 4);
-// largest tile count whose hand-out order is re-sorted at the end of a raycast
+// Raycast tiles are handed out by cost class (march iterations / 8, heaviest
+// first) as measured by the previous raycast, for images of at most
+// kOrderMaxTiles tiles.
 constexpr int kOrderMaxTiles = 1 << 16;
+constexpr int kTileClasses = 16;
+constexpr int kTileHdrInts = 32;  // per side: next, counts[kTileClasses], padding
 constexpr unsigned kFull = 0xffffffffu;
 
 // Sec. 3.2 hash entry.  Bytes 0..7 (x, y, z, flag) form the packed block key
@@ -47,8 +51,6 @@ struct Counters {
     int32_t n_visible;      // per-frame: visible blocks
     int32_t depth_max_bits; // per-frame: largest valid depth (float bits, >= 0)
     int32_t commit_done;    // per-frame: CTAs of the commit kernel that finished
-    int32_t ray_next;       // per-raycast: next 8x4 tile handed to a warp
-    int32_t ray_done;       // per-raycast: CTAs of the raycast kernel that finished
     unsigned long long updated;  // cumulative voxel updates
     unsigned long long visited;  // cumulative voxels visited by integration
     unsigned long long frames;   // cumulative integrated frames
@@ -57,8 +59,7 @@ struct Counters {
 // Offset and size of the per-frame counters cleared at the start of allocation.
 constexpr size_t kFrameCountersOffset = 12;  // n_req
 constexpr size_t kFrameCountersBytes = 20;   // n_req .. commit_done
-constexpr size_t kRayNextOffset = 32;        // ray_next, ray_done
-constexpr size_t kRayNextBytes = 8;
+
 
 struct SceneDev {
     Entry *entries;
@@ -75,8 +76,11 @@ struct SceneDev {
     Counters *ctr;
     uint32_t *range_min;  // per 8x4 tile: nearest / farthest depth (float bits) of covering blocks
     uint32_t *range_max;
-    uint8_t *tile_cost;   // per 8x4 tile: march iterations of the last raycast (+8 with a hit), <= 255
-    int32_t *tile_order;  // tiles ordered by decreasing tile_cost: hand-out order of the next raycast
+    // raycast tile queues, two sides (one written by a raycast, the other
+    // read): per side a header {next tile, count of each cost class} and per
+    // class a list of up to kOrderMaxTiles tiles
+    int32_t *tile_q_hdr;
+    int32_t *tile_q_list;
     int nb, ne, nv;
     int ovf_cap;
     float voxel_size, mu, z_min, z_max;
@@ -200,9 +204,10 @@ struct itm_scene {
     long long range_epoch;
     float range_pose[16];
     itm_intrinsics range_intr;
-    // tile_order is a permutation of the tiles of a tiles_x x tiles_y image
-    // ({0, 0}: none yet)
+    // the tile queues of side 1 - order_side hold every tile of a tiles_x x
+    // tiles_y image ({0, 0}: none yet); the next raycast writes side order_side
     int order_dims[2];
+    int order_side;
 };
 
 // Host helpers implemented in itm_scene.cu.
@@ -221,7 +226,7 @@ cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &i
 cudaError_t launch_integrate(const SceneDev &s, const float *depth, const float *wpx, const Intr &in,
                              const Mat34 &M_d, cudaStream_t st);
 cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, const Mat34 &M_d, float4 *vtx,
-                           float4 *nrm, bool range_ready, int order_dims[2], cudaStream_t st);
+                           float4 *nrm, bool range_ready, int order_dims[2], int &order_side, cudaStream_t st);
 cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 &M_d, uint32_t *rmin, uint32_t *rmax,
                                  cudaStream_t st);
 bool range_fits(const Intr &in);

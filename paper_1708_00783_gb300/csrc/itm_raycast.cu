@@ -64,73 +64,61 @@ __global__ void __launch_bounds__(256) range_kernel(SceneDev s, Mat34 M, Intr in
     }
 }
 
-// Hand-out order of the next raycast: the n tiles by decreasing cost (a
-// counting sort over the 256 cost values, one CTA of 256 threads; the order
-// within one cost value is that of the atomics).
-__device__ void order_tiles_by_cost(const SceneDev &s, int n)
-{
-    __shared__ int bin[256];
-    __shared__ int warp_sum[8];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    bin[tid] = 0;
-    __syncthreads();
-    for (int i = tid; i < n; i += 256) atomicAdd(&bin[255 - (int)__ldcg(&s.tile_cost[i])], 1);
-    __syncthreads();
-    // exclusive scan of the bins, bin 0 (cost 255) first
-    const int c = bin[tid];
-    int x = c;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, x, o);
-        if (lane >= o) x += y;
-    }
-    if (lane == 31) warp_sum[warp] = x;
-    __syncthreads();
-    int base = 0;
-    for (int w = 0; w < warp; ++w) base += warp_sum[w];
-    bin[tid] = base + x - c;
-    __syncthreads();
-    for (int i = tid; i < n; i += 256) {
-        const int p = atomicAdd(&bin[255 - (int)__ldcg(&s.tile_cost[i])], 1);
-        s.tile_order[p] = i;
-    }
-}
-
 // Persistent raycast: each warp takes the next 8x4 tile from a device counter
 // until none is left, so warps that finish early pick up more work instead of
 // idling behind the slowest tiles of a fixed grid.  With use_order the tiles
-// are handed out in tile_order (longest-processing-time first, by the costs
-// of the previous raycast), so the expensive tiles do not start last.  With
-// write_order every tile's cost is recorded and the CTA that finishes last
-// sorts them into tile_order for the next raycast.
+// are handed out from the queues of the previous raycast, heaviest cost class
+// first (longest processing time first), so the expensive tiles do not start
+// last.  With write_order each finished tile is appended to the queue of its
+// cost class for the next raycast.  hdr_w[0] is this raycast's tile counter.
 template <int MODE>
 __global__ void __launch_bounds__(256) raycast_dynamic_kernel(SceneDev s, Intr in, Mat34 T, float4 *__restrict__ vtx,
                                                               float4 *__restrict__ nrm, int max_iter, float tB_m,
                                                               float inv_sv, const uint32_t *__restrict__ rmin,
                                                               const uint32_t *__restrict__ rmax, int tiles_x,
-                                                              int n_tiles, bool use_order, bool write_order)
+                                                              int n_tiles, int32_t *__restrict__ hdr_w,
+                                                              int32_t *__restrict__ list_w,
+                                                              const int32_t *__restrict__ hdr_r,
+                                                              const int32_t *__restrict__ list_r, bool use_order,
+                                                              bool write_order)
 {
-    __shared__ int is_last;
+    // first position of each class slot k (class kTileClasses - 1 - k)
+    __shared__ int first[kTileClasses + 1];
     const int lane = threadIdx.x & 31;
+    if (use_order) {
+        if (threadIdx.x == 0) {
+            int acc = 0;
+            for (int k = 0; k < kTileClasses; ++k) {
+                first[k] = acc;
+                acc += __ldg(&hdr_r[1 + kTileClasses - 1 - k]);
+            }
+            first[kTileClasses] = acc;
+        }
+        __syncthreads();
+        // queues that do not hold every tile once (cannot happen when the
+        // previous raycast covered the same tiles) fall back to raster order
+        use_order = first[kTileClasses] == n_tiles;
+    }
     for (;;) {
         int t = 0;
-        if (lane == 0) t = atomicAdd(&s.ctr->ray_next, 1);
+        if (lane == 0) t = atomicAdd(&hdr_w[0], 1);
         t = __shfl_sync(kFull, t, 0);
-        if (t >= n_tiles) break;
-        // tile_order is rewritten only after every CTA has left this loop
-        const int tile = use_order ? __ldcg(&s.tile_order[t]) : t;
+        if (t >= n_tiles) return;
+        int tile = t;
+        if (use_order) {
+            int k = 0;
+            while (k < kTileClasses - 1 && first[k + 1] <= t) ++k;
+            tile = __ldg(&list_r[(size_t)(kTileClasses - 1 - k) * kOrderMaxTiles + (t - first[k])]);
+            if ((unsigned)tile >= (unsigned)n_tiles) tile = t;
+        }
         const int cost = raycast_warp_tile<MODE, true>(s, in, T, vtx, nrm, max_iter, tB_m, inv_sv, rmin, rmax,
                                                        tiles_x, tile % tiles_x, tile / tiles_x);
-        if (write_order && lane == 0) s.tile_cost[tile] = (uint8_t)cost;
+        if (write_order && lane == 0) {
+            const int c = min(cost >> 3, kTileClasses - 1);
+            const int p = atomicAdd(&hdr_w[1 + c], 1);
+            list_w[(size_t)c * kOrderMaxTiles + p] = tile;
+        }
     }
-    if (!write_order) return;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(&s.ctr->ray_done, 1) == (int)gridDim.x - 1;
-    __syncthreads();
-    if (!is_last) return;
-    __threadfence();
-    order_tiles_by_cost(s, n_tiles);
 }
 
 template <int MODE, bool RANGE>
@@ -172,7 +160,7 @@ cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 
 }
 
 cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, const Mat34 &M_d, float4 *vtx,
-                           float4 *nrm, bool range_ready, int order_dims[2], cudaStream_t st)
+                           float4 *nrm, bool range_ready, int order_dims[2], int &order_side, cudaStream_t st)
 {
     // host-side constants with the same float operations as the oracle
     volatile float span = s.z_max - s.z_min;
@@ -186,8 +174,11 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
     if (range_fits(in)) {
         // the allocation of this frame may have filled the range already
         cudaError_t e = range_ready ? cudaSuccess : launch_raycast_range(s, in, M_d, s.range_min, s.range_max, st);
-        if (e == cudaSuccess)
-            e = cudaMemsetAsync(reinterpret_cast<char *>(s.ctr) + kRayNextOffset, 0, kRayNextBytes, st);
+        const int w = order_side & 1;
+        int32_t *hdr_w = s.tile_q_hdr + w * kTileHdrInts, *list_w = s.tile_q_list + (size_t)w * kTileClasses * kOrderMaxTiles;
+        const int32_t *hdr_r = s.tile_q_hdr + (1 - w) * kTileHdrInts;
+        const int32_t *list_r = s.tile_q_list + (size_t)(1 - w) * kTileClasses * kOrderMaxTiles;
+        if (e == cudaSuccess) e = cudaMemsetAsync(hdr_w, 0, sizeof(int32_t) * kTileHdrInts, st);
         if (e != cudaSuccess) return e;
         static int g_dyn[2] = {0, 0};
         const int mode = s.weight_mode ? 1 : 0;
@@ -205,15 +196,18 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
         const bool use_order = write_order && order_dims[0] == tx && order_dims[1] == ty;
         if (mode == 0)
             raycast_dynamic_kernel<0><<<g, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
-                                                         s.range_max, tx, n_tiles, use_order, write_order);
+                                                         s.range_max, tx, n_tiles, hdr_w, list_w, hdr_r, list_r,
+                                                         use_order, write_order);
         else
             raycast_dynamic_kernel<1><<<g, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
-                                                         s.range_max, tx, n_tiles, use_order, write_order);
+                                                         s.range_max, tx, n_tiles, hdr_w, list_w, hdr_r, list_r,
+                                                         use_order, write_order);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         if (write_order) {
             order_dims[0] = tx;
             order_dims[1] = ty;
+            order_side = 1 - w;
         }
         return cudaSuccess;
     } else {

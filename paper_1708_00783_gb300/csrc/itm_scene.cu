@@ -83,7 +83,7 @@ static void free_dev(SceneDev &d)
 {
     void *ptrs[] = {d.entries, d.req, d.req_list, d.overflow, d.visible, d.block_pos, d.sdf,
                     d.w8, d.w32, d.block_free, d.excess_free, d.ctr, d.range_min, d.range_max,
-                    d.tile_cost, d.tile_order};
+                    d.tile_q_hdr, d.tile_q_list};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     memset(&d, 0, sizeof(d));
@@ -144,8 +144,8 @@ int itm_scene_create(const itm_scene_params *params, itm_scene **out)
     ITM_ALLOC(d.ctr, sizeof(Counters));
     ITM_ALLOC(d.range_min, sizeof(uint32_t) * (size_t)kRangeMaxTiles);
     ITM_ALLOC(d.range_max, sizeof(uint32_t) * (size_t)kRangeMaxTiles);
-    ITM_ALLOC(d.tile_cost, (size_t)kOrderMaxTiles);
-    ITM_ALLOC(d.tile_order, sizeof(int32_t) * (size_t)kOrderMaxTiles);
+    ITM_ALLOC(d.tile_q_hdr, sizeof(int32_t) * 2 * kTileHdrInts);
+    ITM_ALLOC(d.tile_q_list, sizeof(int32_t) * 2 * (size_t)kTileClasses * kOrderMaxTiles);
 #undef ITM_ALLOC
     if (e == cudaSuccess) e = launch_reset(d, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
@@ -238,7 +238,7 @@ int itm_raycast(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16],
     const bool ready = sc->range_epoch == sc->alloc_epoch && memcmp(sc->range_pose, T_wc, sizeof(sc->range_pose)) == 0 &&
                        memcmp(&sc->range_intr, intr, sizeof(itm_intrinsics)) == 0;
     const int r = check_cuda(launch_raycast(sc->d, to_intr(intr), T, M, reinterpret_cast<float4 *>(vertex_dev),
-                                            reinterpret_cast<float4 *>(normal_dev), ready, sc->order_dims, st));
+                                            reinterpret_cast<float4 *>(normal_dev), ready, sc->order_dims, sc->order_side, st));
     if (r == ITM_OK && range_fits(to_intr(intr))) {
         sc->range_epoch = sc->alloc_epoch;
         memcpy(sc->range_pose, T_wc, sizeof(sc->range_pose));
