@@ -7,7 +7,8 @@ imports this package.  The arithmetic lives in ``itm_oracle.c`` (plain C,
 single-threaded, fp32 with every operation rounded separately, as the paper's
 listings are written in float); this module only marshals numpy arrays.
 
-Every function here is pinned by tests in ``tests/test_oracle_pins.py``
+Every function here is pinned by tests in ``tests/test_oracle_pins.py``,
+``tests/test_oracle_conf_pins.py`` and ``tests/test_oracle_combined_pins.py``
 against closed forms, brute force and analytic geometry; see the docstrings
 there for which pin covers which step.
 """
@@ -87,6 +88,12 @@ def _load():
     lib.orc_mlp_loss_grad.restype = ctypes.c_double
     lib.orc_mlp_loss_grad.argtypes = [f32p, f64p, f32p, ctypes.c_int, ctypes.c_int, f64p]
     lib.orc_conf_weights.argtypes = [f32p, ctypes.c_int, ctypes.c_int, f32p, ctypes.c_float, f32p, f32p]
+    lib.orc_set_block.restype = ctypes.c_int
+    lib.orc_set_block.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, f32p, f32p]
+    lib.orc_combined_value.restype = ctypes.c_float
+    lib.orc_combined_value.argtypes = [P, f32p, ctypes.c_int, f32p, P]
+    lib.orc_raycast_combined.restype = ctypes.c_int
+    lib.orc_raycast_combined.argtypes = [P, f32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, f32p, f32p, f32p, f32p]
     _lib = lib
     return lib
 
@@ -180,6 +187,44 @@ class Scene:
         out = np.zeros((nb + ne, 5), dtype=np.int32)
         _load().orc_entries(self.p, out)
         return out
+
+    def set_block(self, b, sdf, w):
+        """Allocate block b (if missing) and set its 512 voxels (x + 8y + 64z)."""
+        sdf = _f32(np.broadcast_to(np.asarray(sdf, dtype=np.float32), (512,)))
+        w = _f32(np.broadcast_to(np.asarray(w, dtype=np.float32), (512,)))
+        if _load().orc_set_block(self.p, int(b[0]), int(b[1]), int(b[2]), sdf, w) != 0:
+            raise RuntimeError("block could not be allocated")
+
+
+# ------------------------------------------------------------- combined map
+
+def _scene_array(scenes):
+    arr = (ctypes.c_void_p * max(1, len(scenes)))(*[sc.p for sc in scenes])
+    return arr
+
+
+def _poses(P, n):
+    P = _f32(P).reshape(n, 4, 4)
+    return np.ascontiguousarray(P.reshape(-1))
+
+
+def combined_value(scenes, P, X):
+    """Sec. 7.2 combined TSDF at world point X over submaps with
+    submap-from-world poses P (n x 4 x 4): (value, weight sum)."""
+    n = len(scenes)
+    den = ctypes.c_float(0.0)
+    v = _load().orc_combined_value(_scene_array(scenes), _poses(P, n), n, _f32(X), ctypes.byref(den))
+    return float(v), float(den.value)
+
+
+def raycast_combined(scenes, P, W, H, intr, T_wc):
+    """Raycast of the combined map of posed submaps: (vertex, normal) maps."""
+    n = len(scenes)
+    vtx = np.zeros((H, W, 4), dtype=np.float32)
+    nrm = np.zeros((H, W, 4), dtype=np.float32)
+    _load().orc_raycast_combined(_scene_array(scenes), _poses(P, n) if n else np.zeros(16, np.float32), n, W, H,
+                                 _f32(intr), _f32(T_wc).ravel(), vtx, nrm)
+    return vtx, nrm
 
 
 # ------------------------------------------------------- learned confidence

@@ -21,6 +21,8 @@
  *                         every intersected block allocated)
  *   orc_integrate         Sec. 4.3 listing computeUpdatedVoxelDepthInfo
  *   orc_raycast           Sec. 4.4 state machine + two trilinear steps
+ *   orc_raycast_combined  Sec. 7.2 combined TSDF of posed submaps, raycast
+ *                         with the Sec. 4.4 state machine
  *   orc_depth_u16_to_f32  Sec. 4 (ViewBuilder: unsigned short -> float depth)
  *
  * Readings taken where the paper is silent (each one is also listed in the
@@ -559,6 +561,223 @@ int orc_raycast(const orc_scene *s, int W, int H, const float intr[4], const flo
         }
     }
     return hits;
+}
+
+/* ------------------------------------------------------------ combined map */
+
+/* Trilinear interpolation of the sdf and of the weight of one submap at its
+ * voxel coordinates q, both over the same eight voxels and in the order of
+ * trilinear(): an unallocated voxel has sdf 1 and weight 0. */
+static void trilinear_fw(const orc_scene *s, const float q[3], float *F, float *Wt)
+{
+    float g0f[3], fr[3];
+    for (int i = 0; i < 3; ++i) {
+        g0f[i] = floorf(q[i]);
+        fr[i] = q[i] - g0f[i];
+    }
+    int x = (int)g0f[0], y = (int)g0f[1], z = (int)g0f[2];
+    float c[8], w[8];
+    for (int k = 0; k < 8; ++k) {
+        int gx = x + (k & 1), gy = y + ((k >> 1) & 1), gz = z + ((k >> 2) & 1);
+        int ptr = lookup(s, gx >> 3, gy >> 3, gz >> 3);
+        if (ptr < 0) {
+            c[k] = 1.0f;
+            w[k] = 0.0f;
+        } else {
+            size_t i = (size_t)ptr * ORC_BLOCK3 + (gx & 7) + 8 * (gy & 7) + 64 * (gz & 7);
+            c[k] = s->sdf[i];
+            w[k] = s->w[i];
+        }
+    }
+    float v[2][8];
+    for (int k = 0; k < 8; ++k) {
+        v[0][k] = c[k];
+        v[1][k] = w[k];
+    }
+    float out[2];
+    for (int m = 0; m < 2; ++m) {
+        float c00 = lerpf(v[m][0], v[m][1], fr[0]);
+        float c10 = lerpf(v[m][2], v[m][3], fr[0]);
+        float c01 = lerpf(v[m][4], v[m][5], fr[0]);
+        float c11 = lerpf(v[m][6], v[m][7], fr[0]);
+        float c0 = lerpf(c00, c10, fr[1]);
+        float c1 = lerpf(c01, c11, fr[1]);
+        out[m] = lerpf(c0, c1, fr[2]);
+    }
+    *F = out[0];
+    *Wt = out[1];
+}
+
+/* Voxel coordinates of world point X in submap i: q = (P_i X) / s, with P_i
+ * (row-major 4x4, submap-from-world) applied row by row as in row_apply.
+ * Returns 0 when a coordinate is out of the representable range. */
+static int submap_coords(const float *P, const float X[3], float inv_s, float q[3])
+{
+    int ok = 1;
+    for (int r = 0; r < 3; ++r) {
+        q[r] = row_apply(P + 4 * r, X[0], X[1], X[2]) * inv_s;
+        ok &= coord_ok(q[r]);
+    }
+    return ok;
+}
+
+/* Is the block of the voxel nearest to X allocated in any submap? */
+static int combined_alloc(const orc_scene *const *S, const float *P, int n, const float X[3], float inv_s)
+{
+    for (int i = 0; i < n; ++i) {
+        float q[3];
+        if (!submap_coords(P + 16 * i, X, inv_s, q)) continue;
+        int bx = ((int)floorf(q[0] + 0.5f)) >> 3, by = ((int)floorf(q[1] + 0.5f)) >> 3,
+            bz = ((int)floorf(q[2] + 0.5f)) >> 3;
+        if (in_i16(bx) && in_i16(by) && in_i16(bz) && lookup(S[i], bx, by, bz) >= 0) return 1;
+    }
+    return 0;
+}
+
+/* Sec. 7.2 combined TSDF at world point X: sum over the submaps (in index
+ * order) of W_i(P_i X) F_i(P_i X), divided by the sum of W_i(P_i X) so that
+ * the value is a TSDF in [-1, 1] and the raycast's step rule keeps its
+ * meaning (the printed sum is not normalised; dividing by a positive number
+ * keeps its zero set).  With no weight anywhere (den = 0) the value is the
+ * unobserved default 1.  *den receives the weight sum. */
+float orc_combined_value(const orc_scene *const *S, const float *P, int n, const float X[3], float *den)
+{
+    const float inv_s = (float)(1.0 / (double)S[0]->voxel_size);
+    float num = 0.0f, dsum = 0.0f;
+    for (int i = 0; i < n; ++i) {
+        float q[3];
+        if (!submap_coords(P + 16 * i, X, inv_s, q)) continue;
+        float F, Wt;
+        trilinear_fw(S[i], q, &F, &Wt);
+        num = num + Wt * F;
+        dsum = dsum + Wt;
+    }
+    if (den) *den = dsum;
+    return dsum > 0.0f ? num / dsum : 1.0f;
+}
+
+/*
+ * Raycast of the combined map of n submaps (Sec. 7.2: the combined TSDF is
+ * never built; it is a view over the submaps during rendering).  P holds n
+ * row-major 4x4 submap-from-world poses; all submaps share voxel size, mu and
+ * the depth range (those of S[0]).  The ray, step sizes, iteration limit,
+ * states and refinement are those of orc_raycast, in world coordinates, with
+ *   allocated(X) = the nearest voxel's block is allocated in some submap,
+ *   F(X)         = orc_combined_value(X).
+ * Normal: central differences of the combined value at X +- s along each
+ * world axis, normalised; none when the gradient is zero or one of the six
+ * samples has no weight in any submap.  Returns the hit count.
+ */
+int orc_raycast_combined(const orc_scene *const *S, const float *P, int n, int W, int H, const float intr[4],
+                         const float T_wc[16], float *vtx, float *nrm)
+{
+    for (size_t k = 0; k < 4 * (size_t)W * H; ++k) vtx[k] = nrm[k] = 0.0f;
+    if (n < 1) return 0;
+    const float fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3];
+    const orc_scene *s0 = S[0];
+    const float vs = s0->voxel_size;
+    const float inv_s = (float)(1.0 / (double)vs);
+    const float B = 8.0f * vs;
+    const float mu = s0->mu;
+    const int max_iter = (int)(4.0f * (s0->z_max - s0->z_min) / vs) + 64;
+    int hits = 0;
+    for (int v = 0; v < H; ++v) {
+        for (int u = 0; u < W; ++u) {
+            size_t o4 = 4 * ((size_t)v * W + u);
+            float dc0 = ((float)u - cx) / fx;
+            float dc1 = ((float)v - cy) / fy;
+            float len = sqrtf((dc0 * dc0 + dc1 * dc1) + 1.0f);
+            float dir[3], org[3];
+            for (int i = 0; i < 3; ++i) {
+                dir[i] = (T_wc[4 * i] * dc0 + T_wc[4 * i + 1] * dc1) + T_wc[4 * i + 2];
+                org[i] = T_wc[4 * i + 3];
+            }
+            const float tB = B / len, tmu = mu / len, ts = vs / len;
+            float t = s0->z_min;
+            int state = SEARCH_BLOCK_COARSE;
+            float X[3];
+            for (int it = 0; it < max_iter && t <= s0->z_max; ++it) {
+                for (int i = 0; i < 3; ++i) X[i] = org[i] + t * dir[i];
+                int alloc = combined_alloc(S, P, n, X, inv_s);
+                if (state == SEARCH_BLOCK_COARSE) {
+                    if (!alloc) {
+                        t = t + tB;
+                    } else {
+                        t = t - tB;
+                        state = SEARCH_BLOCK_FINE;
+                    }
+                    continue;
+                }
+                if (!alloc) {
+                    if (state == SEARCH_BLOCK_FINE) t = t + tmu;
+                    else state = SEARCH_BLOCK_COARSE;
+                    continue;
+                }
+                float F = orc_combined_value(S, P, n, X, NULL);
+                if (state == SEARCH_BLOCK_FINE) {
+                    if (F <= 0.0f) {
+                        state = WRONG_SIDE;
+                        break;
+                    }
+                    state = SEARCH_SURFACE;
+                }
+                if (F <= 0.0f) {
+                    state = BEHIND_SURFACE;
+                    break;
+                }
+                float step = F * tmu;
+                if (step < ts) step = ts;
+                t = t + step;
+            }
+            if (state != BEHIND_SURFACE) continue;
+            for (int r = 0; r < 2; ++r) {
+                for (int i = 0; i < 3; ++i) X[i] = org[i] + t * dir[i];
+                float F = orc_combined_value(S, P, n, X, NULL);
+                t = t + F * tmu;
+            }
+            for (int i = 0; i < 3; ++i) X[i] = org[i] + t * dir[i];
+            vtx[o4] = X[0];
+            vtx[o4 + 1] = X[1];
+            vtx[o4 + 2] = X[2];
+            vtx[o4 + 3] = 1.0f;
+            ++hits;
+            float g[3];
+            int obs = 1;
+            for (int a = 0; a < 3; ++a) {
+                float Xp[3] = {X[0], X[1], X[2]}, Xm[3] = {X[0], X[1], X[2]};
+                Xp[a] = X[a] + vs;
+                Xm[a] = X[a] - vs;
+                float dp, dm;
+                float fp = orc_combined_value(S, P, n, Xp, &dp);
+                float fm = orc_combined_value(S, P, n, Xm, &dm);
+                obs &= dp > 0.0f && dm > 0.0f;
+                g[a] = fp - fm;
+            }
+            float gl = sqrtf((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);
+            if (obs && gl > 0.0f) {
+                nrm[o4] = g[0] / gl;
+                nrm[o4 + 1] = g[1] / gl;
+                nrm[o4 + 2] = g[2] / gl;
+                nrm[o4 + 3] = 1.0f;
+            }
+        }
+    }
+    return hits;
+}
+
+/* Test helper: block (bx, by, bz) allocated if missing, its 512 voxels set
+ * to sdf / w (index x + 8y + 64z).  Returns 0, or -1 when the block could not
+ * be allocated. */
+int orc_set_block(orc_scene *s, int bx, int by, int bz, const float *sdf, const float *w)
+{
+    insert_if_missing(s, bx, by, bz);
+    int ptr = lookup(s, bx, by, bz);
+    if (ptr < 0) return -1;
+    for (int i = 0; i < ORC_BLOCK3; ++i) {
+        s->sdf[(size_t)ptr * ORC_BLOCK3 + i] = sdf[i];
+        s->w[(size_t)ptr * ORC_BLOCK3 + i] = w[i];
+    }
+    return 0;
 }
 
 /* ---------------------------------------------------------- introspection */
