@@ -169,6 +169,31 @@ int itm_raycast(itm_scene *scene, const itm_intrinsics *intr, const float T_wc[1
 int itm_raycast_range(itm_scene *scene, const itm_intrinsics *intr, const float T_wc[16], float *zmin_dev,
                       float *zmax_dev, itm_stream stream);
 
+/* Sec. 7.2 combined map: raycast of the global map formed by n posed
+ * submaps (1 <= n <= ITM_COMBINED_MAX), rendered as a view over them without
+ * building it.  At a world point X the combined TSDF is
+ *   sum_i W_i(P_i X) F_i(P_i X) / sum_i W_i(P_i X)
+ * with F_i and W_i the trilinearly interpolated TSDF and weight of submap i
+ * (an unallocated voxel counts as F = 1, W = 0), summed in index order, and
+ * 1 where the weight sum is 0.  (The paper prints the sum without the
+ * division; dividing by the positive weight sum keeps its zero set and gives
+ * the raycast's step rule a value in [-1, 1].)  The march, refinement and
+ * outputs are those of itm_raycast in world coordinates, "allocated" meaning
+ * that the block of the voxel nearest to P_i X is allocated in some submap;
+ * the normal is the normalised central difference of the combined value at
+ * X +- voxel_size along each world axis, absent (0) when one of the six
+ * samples has weight 0 in every submap.
+ * scenes: host array of n scene handles; all must share voxel_size, mu,
+ * z_min, z_max and weight_mode (else ITM_ERR_ARG).  submap_from_world: host
+ * float[n][16], row-major rigid transforms P_i mapping world coordinates to
+ * submap i's coordinates (the submap's own frame, in which it was fused).
+ * T_wc, vertex_dev, normal_dev: as for itm_raycast (world frame).  The scenes
+ * are only read; the call allocates nothing; asynchronous on stream. */
+#define ITM_COMBINED_MAX 16
+int itm_raycast_combined(itm_scene *const *scenes, const float *submap_from_world, int n,
+                         const itm_intrinsics *intr, const float T_wc[16], float *vertex_dev, float *normal_dev,
+                         itm_stream stream);
+
 /* One frame of the per-frame core: itm_allocate, itm_integrate and (when
  * vertex_dev is not NULL) itm_raycast, on one stream. */
 int itm_process_frame(itm_scene *scene, const float *depth_dev, const itm_intrinsics *intr,

@@ -26,6 +26,7 @@ ITM_NOALLOC_MAX_BLOCKS = 1 << 21
 ITM_MLP_FEATURES, ITM_MLP_HIDDEN, ITM_MLP_PARAMS = 52, 64, 7617
 ITM_MLP_PACKED_BYTES, ITM_MLP_SCRATCH_PER_SAMPLE = 17168, 257
 ITM_BATCH_STAGES = 6
+ITM_COMBINED_MAX = 16
 ST_HASH_FULL, ST_VBA_FULL, ST_RANGE, ST_TIMEOUT, ST_OVERFLOW = 0x1, 0x2, 0x4, 0x8, 0x10
 
 
@@ -100,6 +101,7 @@ def _load():
         "itm_version": (ctypes.c_char_p, []),
         "itm_frame_blocks_noalloc": (I, [P, ip, fp16, F, F, F, F, P, I, P, P]),
         "itm_raycast_range": (I, [P, ip, fp16, P, P, P]),
+        "itm_raycast_combined": (I, [ctypes.POINTER(P), fp16, I, ip, fp16, P, P, P]),
         "itm_mlp_pack": (I, [P, P, P]),
         "itm_conf_weights": (I, [P, ip, F, P, P, P]),
         "itm_conf_features": (I, [P, ip, F, P, I, P, P]),
@@ -211,6 +213,19 @@ def itm_raycast_range(scene, intr, T_wc, zmin, zmax, stream=None):
     a, p = _pose(T_wc)
     _check(_lib.itm_raycast_range(scene, ctypes.byref(intr), p, _ptr(zmin), _ptr(zmax), _stream(stream)),
            "itm_raycast_range")
+
+
+def itm_raycast_combined(scenes, submap_from_world, intr, T_wc, vertex, normal, stream=None):
+    """Raycast of the combined map of posed submaps (scene handles and their
+    submap-from-world poses, n x 4 x 4)."""
+    n = len(scenes)
+    arr = (ctypes.c_void_p * max(1, n))(*scenes)
+    P = np.ascontiguousarray(np.asarray(submap_from_world, dtype=np.float32).reshape(-1))
+    if P.size != 16 * n:
+        raise ValueError("submap_from_world must hold one 4x4 pose per scene")
+    a, p = _pose(T_wc)
+    _check(_lib.itm_raycast_combined(arr, P.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n, ctypes.byref(intr), p,
+                                     _ptr(vertex), _ptr(normal), _stream(stream)), "itm_raycast_combined")
 
 
 def itm_process_frame(scene, depth, intr, T_wc, vertex=None, normal=None, stream=None):

@@ -36,6 +36,7 @@ SOURCES = {
     "itm_noalloc.cu": ["-fmad=false"],
     "itm_conf.cu": [],
     "itm_batch.cu": ["-fmad=false"],
+    "itm_combined.cu": ["-fmad=false"],
 }
 
 

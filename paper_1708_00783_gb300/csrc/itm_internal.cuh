@@ -31,6 +31,7 @@ constexpr int kRangeMaxTiles = (kRangeMaxW / 8) * (kRangeMaxH / 4);
 constexpr int kOrderMaxTiles = 1 << 16;
 constexpr int kTileClasses = 16;
 constexpr int kTileHdrInts = 32;  // per side: next, counts[kTileClasses], padding
+constexpr int kCombinedMax = ITM_COMBINED_MAX;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Sec. 3.2 hash entry.  Bytes 0..7 (x, y, z, flag) form the packed block key
@@ -230,6 +231,8 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
 cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 &M_d, uint32_t *rmin, uint32_t *rmax,
                                  cudaStream_t st);
 bool range_fits(const Intr &in);
+cudaError_t launch_raycast_combined(const SceneDev *subs, const Mat34 *P, int n, const Intr &in, const Mat34 &T_wc,
+                                    float4 *vtx, float4 *nrm, cudaStream_t st);
 cudaError_t launch_depth_u16(const uint16_t *raw, float *out, int64_t n, cudaStream_t st);
 cudaError_t launch_reset(const SceneDev &s, cudaStream_t st);
 }  // namespace itm

@@ -261,6 +261,33 @@ int itm_raycast_range(itm_scene *sc, const itm_intrinsics *intr, const float T_w
                                            reinterpret_cast<uint32_t *>(zmax_dev), st));
 }
 
+int itm_raycast_combined(itm_scene *const *scenes, const float *submap_from_world, int n,
+                         const itm_intrinsics *intr, const float T_wc[16], float *vertex_dev, float *normal_dev,
+                         itm_stream stream)
+{
+    if (!scenes || !submap_from_world || n < 1 || n > ITM_COMBINED_MAX || !valid_intr(intr) || !valid_pose(T_wc) ||
+        !vertex_dev || !normal_dev)
+        return ITM_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(vertex_dev) & 15) || (reinterpret_cast<uintptr_t>(normal_dev) & 15))
+        return ITM_ERR_ARG;
+    SceneDev subs[ITM_COMBINED_MAX];
+    Mat34 P[ITM_COMBINED_MAX];
+    for (int i = 0; i < n; ++i) {
+        const itm_scene *sc = scenes[i];
+        if (!sc || !valid_pose(submap_from_world + 16 * i)) return ITM_ERR_ARG;
+        const itm_scene_params &a = scenes[0]->params, &b = sc->params;
+        if (a.voxel_size != b.voxel_size || a.mu != b.mu || a.z_min != b.z_min || a.z_max != b.z_max ||
+            a.weight_mode != b.weight_mode)
+            return ITM_ERR_ARG;
+        subs[i] = sc->d;
+        pose_rows(submap_from_world + 16 * i, P[i]);
+    }
+    Mat34 T;
+    pose_rows(T_wc, T);
+    return check_cuda(launch_raycast_combined(subs, P, n, to_intr(intr), T, reinterpret_cast<float4 *>(vertex_dev),
+                                              reinterpret_cast<float4 *>(normal_dev), (cudaStream_t)stream));
+}
+
 int itm_process_frame(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
                       float *vertex_dev, float *normal_dev, itm_stream stream)
 {
