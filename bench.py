@@ -369,6 +369,8 @@ def run_batched_section(itm, torch, dev, frames_main, small_frames, n_steps, war
     bad = [sc.status() for sc in sub_scenes + small_scenes if sc.status() != 0]
     itm.itm_batch_destroy(batch)
     default_ms = log[0][2]
+    combined = run_combined_section(itm, torch, dev, stream, sub_scenes, [P for _, P in subs], ci_main,
+                                    frames_main[n_steps // 2][1], H, W, flush)
     return {
         "workload": "16 submaps of the room sequence (2^16..2^20 buckets, relative poses <= 15 deg / 0.5 m, 1-3 "
                     "active per frame) + 64 rooms at 80x60..640x480 with 5-20 mm voxels; one frame per item",
@@ -382,7 +384,39 @@ def run_batched_section(itm, torch, dev, frames_main, small_frames, n_steps, war
         "autotune": {"ctas_per_sm": tuned, "grid_ctas": grids, "tuned_ms_per_step": tuned_ms,
                      "default_ms_per_step": default_ms, "trials": len(log)},
         "status_errors": bad,
+        "combined_render": combined,
     }
+
+
+def run_combined_section(itm, torch, dev, stream, scenes, world_from_submap, ci, T_wc, H, W, flush, reps=10):
+    """Sec. 7.2 combined-map raycast of the fused submaps from a trajectory
+    pose at 640x480: the whole global map (every submap) and the three
+    submaps holding the most blocks."""
+    P = np.stack([np.linalg.inv(x) for x in world_from_submap]).astype(np.float32)
+    blocks = [sc.stats()["allocated_blocks"] for sc in scenes]
+    top = sorted(range(len(scenes)), key=lambda i: -blocks[i])[:3]
+    vtx = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    nrm = torch.empty_like(vtx)
+    out = {"workload": "combined raycast (Sec. 7.2) of the batched section's submaps at 640x480 from the pose of "
+                       "the middle step; L2 flushed between renders", "reps": reps}
+    for name, idx in (("all_submaps", list(range(len(scenes)))), ("top3_submaps", top)):
+        handles = [scenes[i].handle for i in idx]
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                itm.itm_raycast_combined(handles, P[idx], ci, T_wc, vtx, nrm, stream=stream)
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+            for a, b in evs:
+                flush.zero_()
+                a.record(stream)
+                itm.itm_raycast_combined(handles, P[idx], ci, T_wc, vtx, nrm, stream=stream)
+                b.record(stream)
+            torch.cuda.synchronize()
+        ms = float(np.mean([a.elapsed_time(b) for a, b in evs]))
+        hits = int((vtx[..., 3] > 0).sum().item())
+        out[name] = {"submaps": len(idx), "submap_blocks": [blocks[i] for i in idx] if len(idx) <= 3 else sum(blocks),
+                     "ms_per_render": ms, "renders_per_s": 1000.0 / ms, "rays_per_s": H * W / (ms / 1000.0),
+                     "hit_pixels": hits}
+    return out
 
 
 def itm_u16_to_float(raw):

@@ -17,7 +17,18 @@
 // operation that reaches a decision is an explicit round-to-nearest
 // intrinsic in the order above (built with -fmad=false), so the result is
 // that of the same arithmetic on any IEEE machine.  The submaps' tables and
-// poses travel in the kernel's parameter block, so a call allocates nothing.
+// poses travel in the kernels' parameter block, so a call allocates nothing.
+//
+// Search ranges (Sec. 4.4, per submap): first every submap's allocated
+// blocks are projected into the image, each block taken as the region of
+// points whose trilinear stencil reads one of its voxels ([8b - 1.01,
+// 8b + 8.01] voxels), giving per 8x4 tile and submap the nearest and
+// farthest camera depth (written into the submap's own range scratch).  A
+// submap whose range misses the sample's depth has no allocated voxel in
+// the sample's stencil, so its term is an exact zero and is skipped; the
+// coarse steps in front of every range are replayed without probes, and a
+// ray beyond every range in the coarse or fine state can only miss.  The
+// result is therefore the same with or without ranges.
 #include "itm_ops.cuh"
 
 namespace itm {
@@ -26,9 +37,49 @@ namespace {
 
 struct CombinedArgs {
     SceneDev sub[kCombinedMax];
-    Mat34 P[kCombinedMax];  // rows 0..2 of each submap-from-world pose
+    Mat34 P[kCombinedMax];   // rows 0..2 of each submap-from-world pose
+    Mat34 Mc[kCombinedMax];  // rows 0..2 of each camera-from-submap pose
     int n;
+    int use_range;           // tile ranges in sub[i].range_min / range_max
+    int tiles_x, tiles_y;
+    float zc;                // the ranges cover points of camera depth >= zc
 };
+
+// The submap's term may be nonzero at ray depth t (always with no ranges).
+__device__ __forceinline__ bool in_range(const CombinedArgs &A, const float *lo, const float *hi, int i, float t)
+{
+    return !A.use_range || t < A.zc || (t >= lo[i] && t <= hi[i]);
+}
+
+__global__ void __launch_bounds__(256) combined_range_clear_kernel(const CombinedArgs A, int n_tiles)
+{
+    const SceneDev &s = A.sub[blockIdx.y];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_tiles; i += gridDim.x * blockDim.x) {
+        s.range_min[i] = 0xffffffffu;
+        s.range_max[i] = 0u;
+    }
+}
+
+// Stencil-region ranges of the allocated blocks of submap blockIdx.y.
+__global__ void __launch_bounds__(256) combined_range_kernel(const CombinedArgs A, Intr in)
+{
+    const SceneDev &s = A.sub[blockIdx.y];
+    const Mat34 M = A.Mc[blockIdx.y];
+    const int n = min(__ldcg(&s.ctr->block_head), s.nv);
+    const int lane = threadIdx.x & 31;
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; base < n; base += warps * 32) {
+        const int i = base + lane;
+        TileRange r{0, -1, 0, -1, 0.f, 0.f};
+        bool ok = false;
+        if (i < n) {
+            const int ptr = __ldg(&s.block_free[i]);
+            const short4 b = __ldg(&s.block_pos[ptr]);
+            if (b.w) ok = block_tile_range(b, M, in, s.voxel_size, A.zc, A.tiles_x, A.tiles_y, r, 1.01f, 8.01f);
+        }
+        range_rasterize(ok, r, A.tiles_x, s.range_min, s.range_max);
+    }
+}
 
 // Trilinear interpolation of the sdf and of the weight of submap s at its
 // voxel coordinates q (|q| < 262000); unallocated voxels: sdf 1, weight 0.
@@ -94,10 +145,12 @@ __device__ __forceinline__ bool submap_coords(const CombinedArgs &A, int i, cons
     return ok;
 }
 
-// Is the block of the voxel nearest to X allocated in some submap?
-__device__ __forceinline__ bool combined_alloc(const CombinedArgs &A, const float (&X)[3], float inv_s)
+// Is the block of the voxel nearest to X (ray depth t) allocated in some submap?
+__device__ __forceinline__ bool combined_alloc(const CombinedArgs &A, const float (&X)[3], float inv_s, float t,
+                                               const float *lo, const float *hi)
 {
     for (int i = 0; i < A.n; ++i) {
+        if (!in_range(A, lo, hi, i, t)) continue;
         float q[3];
         if (!submap_coords(A, i, X, inv_s, q)) continue;
         const int bx = ((int)floorf(fadd(q[0], 0.5f))) >> 3;
@@ -108,12 +161,16 @@ __device__ __forceinline__ bool combined_alloc(const CombinedArgs &A, const floa
     return false;
 }
 
-// The combined value at X; den receives the weight sum.
+// The combined value at X; den receives the weight sum.  With ray depth t
+// (on_ray) submaps whose range misses t are skipped (their term is 0).
 template <int MODE>
-__device__ __forceinline__ float combined_value(const CombinedArgs &A, const float (&X)[3], float inv_s, float &den)
+__device__ __forceinline__ float combined_value(const CombinedArgs &A, const float (&X)[3], float inv_s, float &den,
+                                                bool on_ray = false, float t = 0.0f, const float *lo = nullptr,
+                                                const float *hi = nullptr)
 {
     float num = 0.0f, dsum = 0.0f;
     for (int i = 0; i < A.n; ++i) {
+        if (on_ray && !in_range(A, lo, hi, i, t)) continue;
         float q[3];
         if (!submap_coords(A, i, X, inv_s, q)) continue;
         float F, Wt;
@@ -131,9 +188,28 @@ __global__ void __launch_bounds__(256) raycast_combined_kernel(const CombinedArg
                                                                int max_iter, float tB_m, float inv_s, float vs,
                                                                float mu, float z_min, float z_max)
 {
+    __shared__ float s_lo[8][kCombinedMax], s_hi[8][kCombinedMax];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int u = (blockIdx.x * 4 + (warp & 3)) * 8 + (lane & 7);
-    const int v = (blockIdx.y * 2 + (warp >> 2)) * 4 + (lane >> 3);
+    const int tix = blockIdx.x * 4 + (warp & 3), tiy = blockIdx.y * 2 + (warp >> 2);
+    if (tix * 8 >= in.W || tiy * 4 >= in.H) return;  // the whole warp's tile is outside
+    const float *lo = s_lo[warp], *hi = s_hi[warp];
+    float T0 = 0.0f, T1 = 3.0e38f;  // nearest and farthest range over the submaps
+    if (A.use_range) {
+        if (lane < A.n) {
+            const int tile = tiy * A.tiles_x + tix;
+            const uint32_t a = __ldg(&A.sub[lane].range_min[tile]), b = __ldg(&A.sub[lane].range_max[tile]);
+            s_lo[warp][lane] = a == 0xffffffffu ? 3.0e38f : __uint_as_float(a);
+            s_hi[warp][lane] = a == 0xffffffffu ? -3.0e38f : __uint_as_float(b);
+        }
+        __syncwarp();
+        T0 = 3.0e38f;
+        T1 = -3.0e38f;
+        for (int i = 0; i < A.n; ++i) {
+            T0 = fminf(T0, lo[i]);
+            T1 = fmaxf(T1, hi[i]);
+        }
+    }
+    const int u = tix * 8 + (lane & 7), v = tiy * 4 + (lane >> 3);
     if (u >= in.W || v >= in.H) return;
     const size_t o = (size_t)v * in.W + u;
     const float dc0 = fdiv(fsub((float)u, in.cx), in.fx);
@@ -148,11 +224,24 @@ __global__ void __launch_bounds__(256) raycast_combined_kernel(const CombinedArg
     const float tB = fdiv(tB_m, len), tmu = fdiv(mu, len), ts = fdiv(vs, len);
     float t = z_min;
     int state = COARSE;
+    int it = 0;
+    if (A.use_range) {
+        if (T1 < T0) {
+            state = MISS;  // no submap has a block near this tile
+        } else {
+            // the oracle's coarse steps in front of every range: t += tB each
+            while (t < T0 && it < max_iter && t <= z_max) {
+                t = fadd(t, tB);
+                ++it;
+            }
+        }
+    }
     float X[3];
-    for (int it = 0; it < max_iter && t <= z_max; ++it) {
+    for (; state <= SURFACE && it < max_iter && t <= z_max; ++it) {
+        if (A.use_range && state != SURFACE && t > T1) break;  // only unallocated space ahead: a miss
 #pragma unroll
         for (int i = 0; i < 3; ++i) X[i] = fadd(org[i], fmul(t, dir[i]));
-        const bool alloc = combined_alloc(A, X, inv_s);
+        const bool alloc = combined_alloc(A, X, inv_s, t, lo, hi);
         if (state == COARSE) {
             if (!alloc) {
                 t = fadd(t, tB);
@@ -168,7 +257,7 @@ __global__ void __launch_bounds__(256) raycast_combined_kernel(const CombinedArg
             continue;
         }
         float den;
-        const float F = combined_value<MODE>(A, X, inv_s, den);
+        const float F = combined_value<MODE>(A, X, inv_s, den, true, t, lo, hi);
         if (state == FINE) {
             if (F <= 0.0f) {
                 state = WRONG;
@@ -191,7 +280,7 @@ __global__ void __launch_bounds__(256) raycast_combined_kernel(const CombinedArg
 #pragma unroll
             for (int i = 0; i < 3; ++i) X[i] = fadd(org[i], fmul(t, dir[i]));
             float den;
-            const float F = combined_value<MODE>(A, X, inv_s, den);
+            const float F = combined_value<MODE>(A, X, inv_s, den, true, t, lo, hi);
             t = fadd(t, fmul(F, tmu));
         }
 #pragma unroll
@@ -227,9 +316,31 @@ cudaError_t launch_raycast_combined(const SceneDev *subs, const Mat34 *P, int n,
     for (int i = 0; i < n; ++i) {
         A.sub[i] = subs[i];
         A.P[i] = P[i];
+        // camera-from-submap = (P_i T_wc)^-1, composed and inverted in fp64
+        double R[3][3], t[3];
+        for (int r = 0; r < 3; ++r) {
+            for (int c = 0; c < 3; ++c) {
+                R[r][c] = 0.0;
+                for (int k = 0; k < 3; ++k) R[r][c] += (double)P[i].m[4 * r + k] * (double)T_wc.m[4 * k + c];
+            }
+            t[r] = (double)P[i].m[4 * r + 3];
+            for (int k = 0; k < 3; ++k) t[r] += (double)P[i].m[4 * r + k] * (double)T_wc.m[4 * k + 3];
+        }
+        for (int r = 0; r < 3; ++r) {
+            double tr = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                A.Mc[i].m[4 * r + k] = (float)R[k][r];
+                tr -= R[k][r] * t[k];
+            }
+            A.Mc[i].m[4 * r + 3] = (float)tr;
+        }
     }
     A.n = n;
     const SceneDev &s0 = subs[0];
+    A.use_range = range_fits(in) ? 1 : 0;
+    A.tiles_x = (in.W + 7) / 8;
+    A.tiles_y = (in.H + 3) / 4;
+    A.zc = s0.z_min - 1e-3f;
     // host-side constants with the same float operations as the oracle
     volatile float span = s0.z_max - s0.z_min;
     volatile float four_span = 4.0f * span;
@@ -237,6 +348,16 @@ cudaError_t launch_raycast_combined(const SceneDev *subs, const Mat34 *P, int n,
     const int max_iter = (int)ratio + 64;
     volatile float tB_m = 8.0f * s0.voxel_size;
     const float inv_s = (float)(1.0 / (double)s0.voxel_size);
+    if (A.use_range) {
+        const int n_tiles = A.tiles_x * A.tiles_y;
+        int dev = 0, sms = 1;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int gx = (n_tiles + 255) / 256 < sms ? (n_tiles + 255) / 256 : sms;
+        combined_range_clear_kernel<<<dim3(gx, n), 256, 0, st>>>(A, n_tiles);
+        const int gr = (4 * sms + n - 1) / n;
+        combined_range_kernel<<<dim3(gr, n), 256, 0, st>>>(A, in);
+    }
     dim3 grid((in.W + 31) / 32, (in.H + 7) / 8);
     if (s0.weight_mode == 0)
         raycast_combined_kernel<0><<<grid, 256, 0, st>>>(A, in, T_wc, vtx, nrm, max_iter, tB_m, inv_s, s0.voxel_size,

@@ -284,6 +284,9 @@ int itm_raycast_combined(itm_scene *const *scenes, const float *submap_from_worl
     }
     Mat34 T;
     pose_rows(T_wc, T);
+    // the combined raycast writes its search ranges into the submaps' range
+    // scratch: their next itm_raycast recomputes its own
+    for (int i = 0; i < n; ++i) scenes[i]->range_epoch = -1;
     return check_cuda(launch_raycast_combined(subs, P, n, to_intr(intr), T, reinterpret_cast<float4 *>(vertex_dev),
                                               reinterpret_cast<float4 *>(normal_dev), (cudaStream_t)stream));
 }
