@@ -122,10 +122,18 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash(name="itm_integrate.cu"):
-    p = os.path.join(ROOT, "paper_1708_00783_gb300", "csrc", name)
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+def integrate_source_hash():
+    """Hash of the integration kernel's source: itm_integrate.cu and the
+    integration section of itm_ops.cuh (from integrate_block's comment up to
+    the raycast section), so edits elsewhere keep a capture valid."""
+    csrc = os.path.join(ROOT, "paper_1708_00783_gb300", "csrc")
+    with open(os.path.join(csrc, "itm_integrate.cu"), "rb") as f:
+        a = f.read()
+    with open(os.path.join(csrc, "itm_ops.cuh"), "rb") as f:
+        ops = f.read()
+    i = ops.index(b"// Block ptr (coordinates b) for thread t")
+    j = ops.index(b"// ---------------------------------------------------------------- raycast")
+    return hashlib.sha256(a + ops[i:j]).hexdigest()[:16]
 
 
 def committed_traffic():
@@ -136,7 +144,7 @@ def committed_traffic():
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("source_sha256_16") != kernel_source_hash() or d.get("ops_sha256_16") != kernel_source_hash("itm_ops.cuh"):
+    if d.get("integrate_source_sha256_16") != integrate_source_hash():
         return None
     return d.get("dram_bytes_per_launch_scaled")
 
