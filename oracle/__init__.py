@@ -94,6 +94,14 @@ def _load():
     lib.orc_combined_value.argtypes = [P, f32p, ctypes.c_int, f32p, P]
     lib.orc_raycast_combined.restype = ctypes.c_int
     lib.orc_raycast_combined.argtypes = [P, f32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, f32p, f32p, f32p, f32p]
+    I = ctypes.c_int
+    lib.orc_depth_halve.argtypes = [f32p, I, I, f32p]
+    lib.orc_icp_reduce.argtypes = [f32p, I, I, f32p, f32p, f32p, f32p, I, I, f32p, f32p, ctypes.c_float, f64p, P]
+    lib.orc_icp_update.restype = I
+    lib.orc_icp_update.argtypes = [f64p, f32p, P]
+    i32p_ = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    lib.orc_track.restype = I
+    lib.orc_track.argtypes = [f32p, I, I, f32p, I, i32p_, f32p, f32p, f32p, I, I, f32p, f32p, f32p]
     _lib = lib
     return lib
 
@@ -272,3 +280,50 @@ def conf_weights(depth, intr, mu, params):
     out = np.zeros((H, W), dtype=np.float32)
     _load().orc_conf_weights(d, W, H, _f32(intr), mu, _f32(params), out)
     return out
+
+
+# ------------------------------------------------------------------ tracking
+
+def depth_halve(depth):
+    """One pyramid level: means of the valid depths of 2x2 pixel blocks."""
+    d = _f32(depth)
+    H, W = d.shape
+    out = np.zeros((H // 2, W // 2), dtype=np.float32)
+    _load().orc_depth_halve(d, W, H, out)
+    return out
+
+
+def icp_reduce(depth, intr, T_g, V, N, intr_r, T_ref, dist_thresh):
+    """Sec. 4.1.1 point-to-plane sums: (sums[29], abs_sums[28]); see
+    orc_icp_reduce for the layout."""
+    d = _f32(depth)
+    H, W = d.shape
+    V, N = _f32(V), _f32(N)
+    Hr, Wr = V.shape[:2]
+    sums = np.zeros(29)
+    abs_sums = np.zeros(28)
+    _load().orc_icp_reduce(d, W, H, _f32(intr), _f32(T_g).ravel(), V.ravel(), N.ravel(), Wr, Hr, _f32(intr_r),
+                           _f32(T_ref).ravel(), float(dist_thresh), sums, abs_sums.ctypes.data)
+    return sums, abs_sums
+
+
+def icp_update(sums, T):
+    """Gauss-Newton step: (new T, step x (6), ok)."""
+    Tn = _f32(T).copy().ravel()
+    x = np.zeros(6)
+    ok = _load().orc_icp_update(np.ascontiguousarray(sums, dtype=np.float64), Tn, x.ctypes.data) == 0
+    return Tn.reshape(4, 4), x, ok
+
+
+def track(depth, intr, iters, thresh, V, N, intr_r, T_ref, T_init):
+    """Coarse-to-fine tracking; iters[l], thresh[l] for pyramid level l
+    (0 = input resolution).  Returns (T, steps)."""
+    d = _f32(depth)
+    H, W = d.shape
+    V, N = _f32(V), _f32(N)
+    Hr, Wr = V.shape[:2]
+    T = _f32(T_init).copy().ravel()
+    it = np.ascontiguousarray(iters, dtype=np.int32)
+    steps = _load().orc_track(d, W, H, _f32(intr), len(it), it, _f32(thresh), V.ravel(), N.ravel(), Wr, Hr,
+                              _f32(intr_r), _f32(T_ref).ravel(), T)
+    return T.reshape(4, 4), int(steps)

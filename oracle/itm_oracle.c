@@ -23,6 +23,8 @@
  *   orc_raycast           Sec. 4.4 state machine + two trilinear steps
  *   orc_raycast_combined  Sec. 7.2 combined TSDF of posed submaps, raycast
  *                         with the Sec. 4.4 state machine
+ *   orc_icp_reduce/track  Sec. 4.1.1 depth tracker: point-to-plane sums over
+ *                         the raycast maps, Gauss-Newton steps, pyramid
  *   orc_depth_u16_to_f32  Sec. 4 (ViewBuilder: unsigned short -> float depth)
  *
  * Readings taken where the paper is silent (each one is also listed in the
@@ -778,6 +780,214 @@ int orc_set_block(orc_scene *s, int bx, int by, int bz, const float *sdf, const 
         s->w[(size_t)ptr * ORC_BLOCK3 + i] = w[i];
     }
     return 0;
+}
+
+/* ---------------------------------------------------------------- tracking */
+
+/* One level of the depth pyramid (Sec. 4.1.1: "a resolution hierarchy of
+ * the depth image").  Output pixel (i, j) of floor(W/2) x floor(H/2) is the
+ * mean of the valid (> 0) depths among input pixels (2i, 2j), (2i+1, 2j),
+ * (2i, 2j+1), (2i+1, 2j+1), summed in that order and divided by their count;
+ * 0 when none is valid. */
+void orc_depth_halve(const float *in, int W, int H, float *out)
+{
+    const int w = W / 2, h = H / 2;
+    for (int j = 0; j < h; ++j) {
+        for (int i = 0; i < w; ++i) {
+            float sum = 0.0f;
+            int n = 0;
+            for (int k = 0; k < 4; ++k) {
+                float d = in[(size_t)(2 * j + (k >> 1)) * W + 2 * i + (k & 1)];
+                if (d > 0.0f) {
+                    sum = sum + d;
+                    ++n;
+                }
+            }
+            out[(size_t)j * w + i] = n > 0 ? sum / (float)n : 0.0f;
+        }
+    }
+}
+
+/*
+ * Sec. 4.1.1 ITMDepthTracker, one evaluation: for each depth pixel p (camera
+ * point d * ((u-cx)/fx, (v-cy)/fy, 1)) mapped to the world by the current
+ * estimate T_g, the projection into the reference view (pose T_ref,
+ * intrinsics intr_r, the raycast maps V and N, world coordinates) picks the
+ * nearest pixel; with both maps valid there and |T_g p - V| <= dist_thresh,
+ * the point-to-plane distance r = (T_g p - V) . N and its derivative with
+ * respect to a small world-frame motion (omega, tau) applied to T_g,
+ * J = (T_g p x N, N), enter the sums.  Per-pixel arithmetic is float, each
+ * operation rounded on its own in the order written; the sums are double.
+ * sums[0..20]: sum J_i J_j (i <= j, row-major upper triangle), sums[21..26]:
+ * sum J_i r, sums[27]: sum r^2, sums[28]: the number of pixels used.
+ * abs_sums (nullable) receives the same sums of absolute values (28).
+ */
+void orc_icp_reduce(const float *depth, int W, int H, const float intr[4], const float T_g[16], const float *V,
+                    const float *N, int Wr, int Hr, const float intr_r[4], const float T_ref[16], float dist_thresh,
+                    double *sums, double *abs_sums)
+{
+    float M[16];
+    rigid_inverse(T_ref, M);
+    const float t2 = dist_thresh * dist_thresh;
+    for (int k = 0; k < 29; ++k) sums[k] = 0.0;
+    if (abs_sums)
+        for (int k = 0; k < 28; ++k) abs_sums[k] = 0.0;
+    for (int v = 0; v < H; ++v) {
+        for (int u = 0; u < W; ++u) {
+            const float d = depth[(size_t)v * W + u];
+            if (!(d > 0.0f)) continue;
+            const float pc[3] = {((float)u - intr[2]) / intr[0] * d, ((float)v - intr[3]) / intr[1] * d, d};
+            float pw[3], pr[3];
+            for (int r = 0; r < 3; ++r) pw[r] = row_apply(T_g + 4 * r, pc[0], pc[1], pc[2]);
+            for (int r = 0; r < 3; ++r) pr[r] = row_apply(M + 4 * r, pw[0], pw[1], pw[2]);
+            if (!(pr[2] > 0.0f)) continue;
+            const float ur = (intr_r[0] * pr[0]) / pr[2] + intr_r[2];
+            const float vr = (intr_r[1] * pr[1]) / pr[2] + intr_r[3];
+            if (!(ur >= 0.0f && ur <= (float)(Wr - 1) && vr >= 0.0f && vr <= (float)(Hr - 1))) continue;
+            const size_t o = 4 * ((size_t)(int)(vr + 0.5f) * Wr + (int)(ur + 0.5f));
+            const float *Vp = V + o, *Np = N + o;
+            if (!(Vp[3] > 0.0f && Np[3] > 0.0f)) continue;
+            const float dx = pw[0] - Vp[0], dy = pw[1] - Vp[1], dz = pw[2] - Vp[2];
+            const float dist2 = (dx * dx + dy * dy) + dz * dz;
+            if (!(dist2 <= t2)) continue;
+            const float res = (dx * Np[0] + dy * Np[1]) + dz * Np[2];
+            const float J[6] = {pw[1] * Np[2] - pw[2] * Np[1], pw[2] * Np[0] - pw[0] * Np[2],
+                                pw[0] * Np[1] - pw[1] * Np[0], Np[0], Np[1], Np[2]};
+            int k = 0;
+            for (int i = 0; i < 6; ++i) {
+                for (int j = i; j < 6; ++j, ++k) {
+                    sums[k] += (double)J[i] * (double)J[j];
+                    if (abs_sums) abs_sums[k] += fabs((double)J[i] * (double)J[j]);
+                }
+            }
+            for (int i = 0; i < 6; ++i) {
+                sums[21 + i] += (double)J[i] * (double)res;
+                if (abs_sums) abs_sums[21 + i] += fabs((double)J[i] * (double)res);
+            }
+            sums[27] += (double)res * (double)res;
+            if (abs_sums) abs_sums[27] += (double)res * (double)res;
+            sums[28] += 1.0;
+        }
+    }
+}
+
+/*
+ * Gauss-Newton step from the sums (the host side of the tracker): solve
+ * H x = -g (H = sum J J^T, g = sum J r) by Cholesky in double, then apply the
+ * motion x = (omega, tau) on the world side: T <- [R(omega) | tau] T with
+ * R(omega) the rotation by |omega| about omega / |omega| (Rodrigues), in
+ * double, rounded to float once.  Returns 0, or -1 (T unchanged) when H is
+ * not positive definite.  x (nullable) receives the step.
+ */
+int orc_icp_update(const double *sums, float T[16], double *x_out)
+{
+    double A[6][6], b[6];
+    int k = 0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j, ++k) A[i][j] = A[j][i] = sums[k];
+    for (int i = 0; i < 6; ++i) b[i] = -sums[21 + i];
+    double L[6][6] = {{0}};
+    for (int i = 0; i < 6; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double acc = A[i][j];
+            for (int m = 0; m < j; ++m) acc -= L[i][m] * L[j][m];
+            if (i == j) {
+                if (!(acc > 0.0)) return -1;
+                L[i][i] = sqrt(acc);
+            } else {
+                L[i][j] = acc / L[j][j];
+            }
+        }
+    }
+    double y[6], x[6];
+    for (int i = 0; i < 6; ++i) {
+        double acc = b[i];
+        for (int m = 0; m < i; ++m) acc -= L[i][m] * y[m];
+        y[i] = acc / L[i][i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double acc = y[i];
+        for (int m = i + 1; m < 6; ++m) acc -= L[m][i] * x[m];
+        x[i] = acc / L[i][i];
+    }
+    if (x_out)
+        for (int i = 0; i < 6; ++i) x_out[i] = x[i];
+    const double th = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    const double K[3][3] = {{0.0, -x[2], x[1]}, {x[2], 0.0, -x[0]}, {-x[1], x[0], 0.0}};
+    double K2[3][3], R[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            K2[i][j] = 0.0;
+            for (int m = 0; m < 3; ++m) K2[i][j] += K[i][m] * K[m][j];
+        }
+    const double a = th > 1e-12 ? sin(th) / th : 1.0;
+    const double c = th > 1e-12 ? (1.0 - cos(th)) / (th * th) : 0.5;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R[i][j] = (i == j ? 1.0 : 0.0) + a * K[i][j] + c * K2[i][j];
+    double out[12];
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            double acc = 0.0;
+            for (int m = 0; m < 3; ++m) acc += R[i][m] * (double)T[4 * m + j];
+            out[4 * i + j] = acc;
+        }
+        double acc = x[3 + i];
+        for (int m = 0; m < 3; ++m) acc += R[i][m] * (double)T[4 * m + 3];
+        out[4 * i + 3] = acc;
+    }
+    for (int i = 0; i < 12; ++i) T[i] = (float)out[i];
+    T[12] = T[13] = T[14] = 0.0f;
+    T[15] = 1.0f;
+    return 0;
+}
+
+/* Intrinsics of the next pyramid level: pixel i covers pixels 2i, 2i+1, so
+ * the focal lengths halve and the centre maps as c -> (c - 0.5) / 2. */
+static void halve_intr(const float in[4], float out[4])
+{
+    out[0] = in[0] / 2.0f;
+    out[1] = in[1] / 2.0f;
+    out[2] = (in[2] - 0.5f) / 2.0f;
+    out[3] = (in[3] - 0.5f) / 2.0f;
+}
+
+/*
+ * Coarse-to-fine tracking (Sec. 4.1.1): levels 0 (the input) .. L-1 of the
+ * pyramid; from level L-1 down to 0, iters[l] Gauss-Newton steps with
+ * outlier distance thresh[l].  A level stops early when fewer than 6 pixels
+ * are used or the step cannot be solved.  T (in/out) is the camera-to-world
+ * estimate.  Returns the number of steps applied.
+ */
+int orc_track(const float *depth, int W, int H, const float intr[4], int L, const int *iters, const float *thresh,
+              const float *V, const float *N, int Wr, int Hr, const float intr_r[4], const float T_ref[16], float T[16])
+{
+    float *lev[8];
+    int lw[8], lh[8];
+    float li[8][4];
+    if (L < 1 || L > 8) return 0;
+    lev[0] = (float *)depth;
+    lw[0] = W;
+    lh[0] = H;
+    for (int k = 0; k < 4; ++k) li[0][k] = intr[k];
+    for (int l = 1; l < L; ++l) {
+        lw[l] = lw[l - 1] / 2;
+        lh[l] = lh[l - 1] / 2;
+        lev[l] = (float *)malloc(sizeof(float) * (size_t)(lw[l] > 0 ? lw[l] : 1) * (size_t)(lh[l] > 0 ? lh[l] : 1));
+        orc_depth_halve(lev[l - 1], lw[l - 1], lh[l - 1], lev[l]);
+        halve_intr(li[l - 1], li[l]);
+    }
+    int steps = 0;
+    double sums[29];
+    for (int l = L - 1; l >= 0; --l) {
+        for (int it = 0; it < iters[l]; ++it) {
+            orc_icp_reduce(lev[l], lw[l], lh[l], li[l], T, V, N, Wr, Hr, intr_r, T_ref, thresh[l], sums, NULL);
+            if (sums[28] < 6.0) break;
+            if (orc_icp_update(sums, T, NULL) != 0) break;
+            ++steps;
+        }
+    }
+    for (int l = 1; l < L; ++l) free(lev[l]);
+    return steps;
 }
 
 /* ---------------------------------------------------------- introspection */
