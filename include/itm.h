@@ -50,6 +50,7 @@ enum {
     ITM_ERR_TIMEOUT = 6,   /* status: a bounded device-side wait gave up */
     ITM_ERR_OVERFLOW = 7,  /* status: a per-frame work list overflowed */
     ITM_ERR_TOO_LARGE = 8, /* the input could exceed a fixed-size buffer of the call */
+    ITM_ERR_SINGULAR = 9,  /* a tracking step has no unique solution (fewer than 6 constrained motions) */
 };
 
 /* Sticky status bits (itm_stats.status). */
@@ -193,6 +194,72 @@ int itm_raycast_range(itm_scene *scene, const itm_intrinsics *intr, const float 
 int itm_raycast_combined(itm_scene *const *scenes, const float *submap_from_world, int n,
                          const itm_intrinsics *intr, const float T_wc[16], float *vertex_dev, float *normal_dev,
                          itm_stream stream);
+
+/* ---------------------------------------------------------------------
+ * Sec. 4.1.1 depth tracker (ITMDepthTracker): align a depth frame to the
+ * vertex and normal maps of an itm_raycast by minimising the sum of squared
+ * point-to-plane distances, over a resolution hierarchy of the depth image.
+ */
+
+/* One level of the depth pyramid: out_dev[j][i] (floor(width/2) x
+ * floor(height/2), device float) is the mean of the valid (> 0) depths of
+ * in_dev's pixels (2i, 2j), (2i+1, 2j), (2i, 2j+1), (2i+1, 2j+1), summed in
+ * that order and divided once by their count; 0 when none is valid.  The
+ * level's intrinsics are fx/2, fy/2, (cx - 1/2)/2, (cy - 1/2)/2. */
+int itm_depth_halve(const float *in_dev, int width, int height, float *out_dev, itm_stream stream);
+
+#define ITM_ICP_SUMS 29
+#define ITM_ICP_WORK_DOUBLES (ITM_ICP_SUMS * 1025)
+
+/* One evaluation of the tracker's linear system.  For each pixel of
+ * depth_dev (device float[height][width] of intr) with depth d > 0, the
+ * camera point d ((u-cx)/fx, (v-cy)/fy, 1) is mapped to the world by the
+ * estimate T_g (camera-to-world) and projected into the reference view
+ * (pose T_ref, intrinsics ref_intr) of the maps vertex_dev / normal_dev
+ * (device float4[ref height][ref width], world coordinates, w > 0 valid, as
+ * written by itm_raycast); at the nearest pixel, when both maps are valid and
+ * |T_g p - V| <= dist_thresh, the residual r = (T_g p - V) . N and its
+ * derivative J = (T_g p x N, N) with respect to a small world-frame motion
+ * (rotation omega, translation tau) enter the sums.  Per-pixel arithmetic
+ * is float with every operation rounded on its own; a thread sums its pixels
+ * in float, the rest of the reduction is double, in a fixed order.
+ * work_dev: device double[ITM_ICP_WORK_DOUBLES] (8-byte aligned); on return
+ * (asynchronous) work_dev[0..28] hold sum J_i J_j (i <= j, row-major upper
+ * triangle, 21), sum J_i r (6), sum r^2 and the number of pixels used. */
+int itm_icp_reduce(const float *depth_dev, const itm_intrinsics *intr, const float T_g[16],
+                   const float *vertex_dev, const float *normal_dev, const itm_intrinsics *ref_intr,
+                   const float T_ref[16], float dist_thresh, double *work_dev, itm_stream stream);
+
+/* Host: one Gauss-Newton step from the sums (HOST double[29], as written by
+ * itm_icp_reduce): solve H x = -g by Cholesky in double and apply the motion
+ * x = (omega, tau) on the world side, T <- [R(omega) | tau] T (Rodrigues).
+ * T_inout: host float[16]; step_out (nullable): host double[6].  Returns
+ * ITM_ERR_SINGULAR (T unchanged) when fewer than 6 pixels were used or H is
+ * not positive definite. */
+int itm_icp_step(const double *sums, float T_inout[16], double *step_out);
+
+#define ITM_TRACK_MAX_LEVELS 8
+
+/* Bytes of device scratch itm_track_depth needs for an image of width x
+ * height and the given number of levels. */
+size_t itm_track_scratch_bytes(int width, int height, int levels);
+
+/* Coarse-to-fine tracking of one depth frame (device float[height][width]
+ * of intr) against the maps of a raycast from T_ref: pyramid levels
+ * 0 (input) .. levels-1 (1 <= levels <= ITM_TRACK_MAX_LEVELS); from the
+ * coarsest level down, iters[l] steps (itm_icp_reduce + the step of
+ * itm_icp_step, taken on the device in double) with outlier distance
+ * dist_thresh[l] (host arrays of levels entries); a level ends early when a
+ * step has no unique solution.  T_inout: host float[16], the initial
+ * camera-to-world estimate, replaced by the result; steps_out (nullable):
+ * the steps applied.  scratch_dev: device memory of
+ * itm_track_scratch_bytes(width, height, levels) bytes, 256-byte aligned,
+ * owned by the caller, contents irrelevant.  Synchronises the stream once at
+ * the end (no host round trip per step). */
+int itm_track_depth(const float *depth_dev, const itm_intrinsics *intr, int levels, const int *iters,
+                    const float *dist_thresh, const float *vertex_dev, const float *normal_dev,
+                    const itm_intrinsics *ref_intr, const float T_ref[16], float T_inout[16], int *steps_out,
+                    void *scratch_dev, itm_stream stream);
 
 /* One frame of the per-frame core: itm_allocate, itm_integrate and (when
  * vertex_dev is not NULL) itm_raycast, on one stream. */

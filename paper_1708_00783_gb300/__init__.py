@@ -27,6 +27,9 @@ ITM_MLP_FEATURES, ITM_MLP_HIDDEN, ITM_MLP_PARAMS = 52, 64, 7617
 ITM_MLP_PACKED_BYTES, ITM_MLP_SCRATCH_PER_SAMPLE = 17168, 257
 ITM_BATCH_STAGES = 6
 ITM_COMBINED_MAX = 16
+ITM_ICP_SUMS = 29
+ITM_ICP_WORK_DOUBLES = ITM_ICP_SUMS * 1025
+ITM_TRACK_MAX_LEVELS = 8
 ST_HASH_FULL, ST_VBA_FULL, ST_RANGE, ST_TIMEOUT, ST_OVERFLOW = 0x1, 0x2, 0x4, 0x8, 0x10
 
 
@@ -102,6 +105,11 @@ def _load():
         "itm_frame_blocks_noalloc": (I, [P, ip, fp16, F, F, F, F, P, I, P, P]),
         "itm_raycast_range": (I, [P, ip, fp16, P, P, P]),
         "itm_raycast_combined": (I, [ctypes.POINTER(P), fp16, I, ip, fp16, P, P, P]),
+        "itm_depth_halve": (I, [P, I, I, P, P]),
+        "itm_icp_reduce": (I, [P, ip, fp16, P, P, ip, fp16, F, P, P]),
+        "itm_icp_step": (I, [ctypes.POINTER(ctypes.c_double), fp16, ctypes.POINTER(ctypes.c_double)]),
+        "itm_track_scratch_bytes": (ctypes.c_size_t, [I, I, I]),
+        "itm_track_depth": (I, [P, ip, I, ctypes.POINTER(I), fp16, P, P, ip, fp16, fp16, ctypes.POINTER(I), P, P]),
         "itm_mlp_pack": (I, [P, P, P]),
         "itm_conf_weights": (I, [P, ip, F, P, P, P]),
         "itm_conf_features": (I, [P, ip, F, P, I, P, P]),
@@ -226,6 +234,51 @@ def itm_raycast_combined(scenes, submap_from_world, intr, T_wc, vertex, normal, 
     a, p = _pose(T_wc)
     _check(_lib.itm_raycast_combined(arr, P.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n, ctypes.byref(intr), p,
                                      _ptr(vertex), _ptr(normal), _stream(stream)), "itm_raycast_combined")
+
+
+def itm_depth_halve(depth_in, width, height, depth_out, stream=None):
+    _check(_lib.itm_depth_halve(_ptr(depth_in), int(width), int(height), _ptr(depth_out), _stream(stream)),
+           "itm_depth_halve")
+
+
+def itm_icp_reduce(depth, intr, T_g, vertex, normal, ref_intr, T_ref, dist_thresh, work, stream=None):
+    a, p = _pose(T_g)
+    b, q = _pose(T_ref)
+    _check(_lib.itm_icp_reduce(_ptr(depth), ctypes.byref(intr), p, _ptr(vertex), _ptr(normal), ctypes.byref(ref_intr),
+                               q, float(dist_thresh), _ptr(work), _stream(stream)), "itm_icp_reduce")
+
+
+def itm_icp_step(sums, T):
+    """Host Gauss-Newton step: (new T, step (6)); raises ItmError when the
+    system has no unique solution."""
+    s = np.ascontiguousarray(np.asarray(sums, dtype=np.float64).reshape(ITM_ICP_SUMS))
+    a, p = _pose(T)
+    a = a.copy()
+    x = np.zeros(6)
+    _check(_lib.itm_icp_step(s.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             a.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                             x.ctypes.data_as(ctypes.POINTER(ctypes.c_double))), "itm_icp_step")
+    return a.reshape(4, 4), x
+
+
+def itm_track_scratch_bytes(width, height, levels):
+    return int(_lib.itm_track_scratch_bytes(int(width), int(height), int(levels)))
+
+
+def itm_track_depth(depth, intr, iters, dist_thresh, vertex, normal, ref_intr, T_ref, T_init, scratch, stream=None):
+    """Coarse-to-fine depth tracking; iters[l], dist_thresh[l] per pyramid
+    level (0 = input resolution).  Returns (T, steps)."""
+    L = len(iters)
+    it = (ctypes.c_int * L)(*[int(x) for x in iters])
+    th = np.ascontiguousarray(np.asarray(dist_thresh, dtype=np.float32).reshape(L))
+    b, q = _pose(T_ref)
+    T = np.ascontiguousarray(np.asarray(T_init, dtype=np.float32).reshape(16)).copy()
+    steps = ctypes.c_int(0)
+    _check(_lib.itm_track_depth(_ptr(depth), ctypes.byref(intr), L, it, th.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                _ptr(vertex), _ptr(normal), ctypes.byref(ref_intr), q,
+                                T.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(steps), _ptr(scratch),
+                                _stream(stream)), "itm_track_depth")
+    return T.reshape(4, 4), steps.value
 
 
 def itm_process_frame(scene, depth, intr, T_wc, vertex=None, normal=None, stream=None):

@@ -37,6 +37,7 @@ SOURCES = {
     "itm_conf.cu": [],
     "itm_batch.cu": ["-fmad=false"],
     "itm_combined.cu": ["-fmad=false"],
+    "itm_track.cu": ["-fmad=false"],
 }
 
 

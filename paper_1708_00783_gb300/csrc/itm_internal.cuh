@@ -32,6 +32,10 @@ constexpr int kOrderMaxTiles = 1 << 16;
 constexpr int kTileClasses = 16;
 constexpr int kTileHdrInts = 32;  // per side: next, counts[kTileClasses], padding
 constexpr int kCombinedMax = ITM_COMBINED_MAX;
+constexpr int kIcpSums = ITM_ICP_SUMS;
+constexpr int kIcpWorkDoubles = ITM_ICP_WORK_DOUBLES;
+constexpr int kIcpMaxPartials = ITM_ICP_WORK_DOUBLES / ITM_ICP_SUMS - 1;
+constexpr int kTrackMaxLevels = ITM_TRACK_MAX_LEVELS;
 constexpr unsigned kFull = 0xffffffffu;
 
 // Sec. 3.2 hash entry.  Bytes 0..7 (x, y, z, flag) form the packed block key
@@ -231,6 +235,13 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
 cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 &M_d, uint32_t *rmin, uint32_t *rmax,
                                  cudaStream_t st);
 bool range_fits(const Intr &in);
+cudaError_t launch_depth_halve(const float *in, int W, int H, float *out, cudaStream_t st);
+cudaError_t launch_icp_reduce(const float *depth, const Intr &in, const Mat34 &T_g, const float4 *V, const float4 *N,
+                              const Intr &ref, const Mat34 &M_ref, float dist_thresh, double *work, cudaStream_t st);
+size_t track_scratch_bytes(int W, int H, int levels);
+cudaError_t launch_track(const float *depth, const Intr &in0, int levels, const int *iters, const float *thresh,
+                         const float4 *V, const float4 *N, const Intr &ref, const Mat34 &M_ref, float T[16],
+                         int *steps, void *scratch, cudaStream_t st);
 cudaError_t launch_raycast_combined(const SceneDev *subs, const Mat34 *P, int n, const Intr &in, const Mat34 &T_wc,
                                     float4 *vtx, float4 *nrm, cudaStream_t st);
 cudaError_t launch_depth_u16(const uint16_t *raw, float *out, int64_t n, cudaStream_t st);

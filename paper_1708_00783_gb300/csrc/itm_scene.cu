@@ -291,6 +291,122 @@ int itm_raycast_combined(itm_scene *const *scenes, const float *submap_from_worl
                                               reinterpret_cast<float4 *>(normal_dev), (cudaStream_t)stream));
 }
 
+int itm_depth_halve(const float *in_dev, int width, int height, float *out_dev, itm_stream stream)
+{
+    if (!in_dev || !out_dev || width < 2 || height < 2 || (long long)width * height >= (1ll << 30)) return ITM_ERR_ARG;
+    return check_cuda(launch_depth_halve(in_dev, width, height, out_dev, (cudaStream_t)stream));
+}
+
+static int valid_thresh(float t) { return t > 0.0f && isfinite(t); }
+
+int itm_icp_reduce(const float *depth_dev, const itm_intrinsics *intr, const float T_g[16], const float *vertex_dev,
+                   const float *normal_dev, const itm_intrinsics *ref_intr, const float T_ref[16], float dist_thresh,
+                   double *work_dev, itm_stream stream)
+{
+    if (!depth_dev || !valid_intr(intr) || !valid_pose(T_g) || !vertex_dev || !normal_dev || !valid_intr(ref_intr) ||
+        !valid_pose(T_ref) || !valid_thresh(dist_thresh) || !work_dev)
+        return ITM_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(vertex_dev) & 15) || (reinterpret_cast<uintptr_t>(normal_dev) & 15) ||
+        (reinterpret_cast<uintptr_t>(work_dev) & 7))
+        return ITM_ERR_ARG;
+    Mat34 T, M;
+    pose_rows(T_g, T);
+    rigid_inverse_rows(T_ref, M);
+    return check_cuda(launch_icp_reduce(depth_dev, to_intr(intr), T, reinterpret_cast<const float4 *>(vertex_dev),
+                                        reinterpret_cast<const float4 *>(normal_dev), to_intr(ref_intr), M,
+                                        dist_thresh, work_dev, (cudaStream_t)stream));
+}
+
+int itm_icp_step(const double *sums, float T_inout[16], double *step_out)
+{
+    if (!sums || !T_inout || !valid_pose(T_inout)) return ITM_ERR_ARG;
+    if (!(sums[28] >= 6.0)) return ITM_ERR_SINGULAR;
+    double A[6][6], L[6][6] = {{0.0}}, y[6], x[6];
+    int k = 0;
+    for (int i = 0; i < 6; ++i)
+        for (int j = i; j < 6; ++j, ++k) A[i][j] = A[j][i] = sums[k];
+    for (int i = 0; i < 6; ++i) {
+        for (int j = 0; j <= i; ++j) {
+            double a = A[i][j];
+            for (int m = 0; m < j; ++m) a -= L[i][m] * L[j][m];
+            if (i == j) {
+                if (!(a > 0.0)) return ITM_ERR_SINGULAR;
+                L[i][i] = sqrt(a);
+            } else {
+                L[i][j] = a / L[j][j];
+            }
+        }
+    }
+    for (int i = 0; i < 6; ++i) {
+        double a = -sums[21 + i];
+        for (int m = 0; m < i; ++m) a -= L[i][m] * y[m];
+        y[i] = a / L[i][i];
+    }
+    for (int i = 5; i >= 0; --i) {
+        double a = y[i];
+        for (int m = i + 1; m < 6; ++m) a -= L[m][i] * x[m];
+        x[i] = a / L[i][i];
+    }
+    const double th = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+    const double s1 = th > 1e-12 ? sin(th) / th : 1.0;
+    const double s2 = th > 1e-12 ? (1.0 - cos(th)) / (th * th) : 0.5;
+    const double K[3][3] = {{0.0, -x[2], x[1]}, {x[2], 0.0, -x[0]}, {-x[1], x[0], 0.0}};
+    double R[3][3], Tn[12];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double k2 = 0.0;
+            for (int m = 0; m < 3; ++m) k2 += K[i][m] * K[m][j];
+            R[i][j] = (i == j ? 1.0 : 0.0) + s1 * K[i][j] + s2 * k2;
+        }
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 3; ++j) {
+            double a = 0.0;
+            for (int m = 0; m < 3; ++m) a += R[i][m] * (double)T_inout[4 * m + j];
+            Tn[4 * i + j] = a;
+        }
+        double a = x[3 + i];
+        for (int m = 0; m < 3; ++m) a += R[i][m] * (double)T_inout[4 * m + 3];
+        Tn[4 * i + 3] = a;
+    }
+    for (int i = 0; i < 12; ++i) T_inout[i] = (float)Tn[i];
+    T_inout[12] = T_inout[13] = T_inout[14] = 0.0f;
+    T_inout[15] = 1.0f;
+    if (step_out)
+        for (int i = 0; i < 6; ++i) step_out[i] = x[i];
+    return ITM_OK;
+}
+
+size_t itm_track_scratch_bytes(int width, int height, int levels)
+{
+    if (width < 1 || height < 1 || levels < 1 || levels > ITM_TRACK_MAX_LEVELS) return 0;
+    return track_scratch_bytes(width, height, levels);
+}
+
+int itm_track_depth(const float *depth_dev, const itm_intrinsics *intr, int levels, const int *iters,
+                    const float *dist_thresh, const float *vertex_dev, const float *normal_dev,
+                    const itm_intrinsics *ref_intr, const float T_ref[16], float T_inout[16], int *steps_out,
+                    void *scratch_dev, itm_stream stream)
+{
+    if (!depth_dev || !valid_intr(intr) || levels < 1 || levels > ITM_TRACK_MAX_LEVELS || !iters || !dist_thresh ||
+        !vertex_dev || !normal_dev || !valid_intr(ref_intr) || !valid_pose(T_ref) || !T_inout ||
+        !valid_pose(T_inout) || !scratch_dev)
+        return ITM_ERR_ARG;
+    if ((reinterpret_cast<uintptr_t>(vertex_dev) & 15) || (reinterpret_cast<uintptr_t>(normal_dev) & 15) ||
+        (reinterpret_cast<uintptr_t>(scratch_dev) & 255))
+        return ITM_ERR_ARG;
+    for (int l = 0; l < levels; ++l)
+        if (iters[l] < 0 || iters[l] > 1000 || !valid_thresh(dist_thresh[l])) return ITM_ERR_ARG;
+    Mat34 M;
+    rigid_inverse_rows(T_ref, M);
+    int steps = 0;
+    const int r = check_cuda(launch_track(depth_dev, to_intr(intr), levels, iters, dist_thresh,
+                                          reinterpret_cast<const float4 *>(vertex_dev),
+                                          reinterpret_cast<const float4 *>(normal_dev), to_intr(ref_intr), M, T_inout,
+                                          &steps, scratch_dev, (cudaStream_t)stream));
+    if (r == ITM_OK && steps_out) *steps_out = steps;
+    return r;
+}
+
 int itm_process_frame(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
                       float *vertex_dev, float *normal_dev, itm_stream stream)
 {
