@@ -427,6 +427,68 @@ def run_combined_section(itm, torch, dev, stream, scenes, world_from_submap, ci,
     return out
 
 
+TRACK_ITERS = [10, 5, 4]          # pyramid level 0 (640x480), 1, 2
+TRACK_THRESH = [0.05, 0.1, 0.2]   # outlier distance per level, metres
+
+
+def run_tracking_section(itm, torch, dev, stream, scene, raw_dev, poses, ci, depth, vtx, nrm, flush, n_pix, H, W,
+                         frames):
+    """Sec. 4.1.1 depth tracker on the fused room: frame k tracked against the
+    raycast of the volume from frame k-1's pose, started there; the whole
+    coarse-to-fine track (pyramid, 19 steps with the solve on the device, one
+    host sync) timed with CUDA events; the full-resolution reduction timed
+    alone with the L2 flushed, for its HBM bandwidth."""
+    nbytes = itm.itm_track_scratch_bytes(W, H, len(TRACK_ITERS))
+    scratch = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+    sp = scratch.data_ptr() + (-scratch.data_ptr()) % 256
+    work = torch.zeros(itm.ITM_ICP_WORK_DOUBLES, dtype=torch.float64, device=dev)
+    d_k = torch.empty_like(depth)
+    track_ms, red_ms, err_t, err_a, used, valid = [], [], [], [], [], []
+    for k in frames:
+        T_prev, T_true = poses[k - 1], poses[k]
+        itm.itm_raycast(scene.handle, ci, T_prev, vtx, nrm, stream)
+        itm.itm_depth_u16_to_f32(raw_dev[k], d_k, n_pix, stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        flush.zero_()
+        a.record(stream)
+        T, steps = itm.itm_track_depth(d_k, ci, TRACK_ITERS, TRACK_THRESH, vtx, nrm, ci, T_prev, T_prev, sp, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        track_ms.append(a.elapsed_time(b))
+        R = np.asarray(T, np.float64)[:3, :3].T @ np.asarray(T_true, np.float64)[:3, :3]
+        err_t.append(float(np.linalg.norm(np.asarray(T, np.float64)[:3, 3] - T_true[:3, 3])))
+        err_a.append(float(np.degrees(np.arccos(np.clip((np.trace(R) - 1) / 2, -1, 1)))))
+        flush.zero_()
+        a.record(stream)
+        itm.itm_icp_reduce(d_k, ci, T_prev, vtx, nrm, ci, T_prev, TRACK_THRESH[0], work, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        red_ms.append(a.elapsed_time(b))
+        used.append(float(work[28].item()))
+        valid.append(float((d_k > 0).sum().item()))
+    red = float(np.mean(red_ms))
+    # algorithmic bytes of one full-resolution reduction: the depth frame, and
+    # one vertex and one normal float4 per valid depth pixel
+    alg = 4.0 * n_pix + 32.0 * float(np.mean(valid))
+    peak, peak_kind = load_peaks()
+    return {
+        "workload": "frames %d..%d of the room, each tracked against the raycast of the fused volume from the "
+                    "previous frame's pose (started there), 640x480, levels %s, outlier distances %s m; L2 flushed "
+                    "before each timed call" % (frames[0], frames[-1], TRACK_ITERS, TRACK_THRESH),
+        "frames": len(frames),
+        "ms_per_track": float(np.mean(track_ms)),
+        "tracks_per_s": 1000.0 / float(np.mean(track_ms)),
+        "steps_per_track": sum(TRACK_ITERS),
+        "translation_error_mm_mean": 1000.0 * float(np.mean(err_t)),
+        "rotation_error_deg_mean": float(np.mean(err_a)),
+        "reduce_full_res": {"kernel": "icp_partial_kernel + icp_solve_kernel", "bound": "hbm",
+                            "ms": red, "pixels_used_mean": float(np.mean(used)),
+                            "algorithmic_bytes": alg, "achieved_gbs": alg / (red / 1000.0) / 1e9,
+                            "peak": peak, "peak_kind": peak_kind, "frac": alg / (red / 1000.0) / 1e9 / peak},
+    }
+
+
 def itm_u16_to_float(raw):
     """Host conversion used only to stage the batched section's inputs (the
     timed per-frame path converts on the device)."""
@@ -614,6 +676,11 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = load_peaks()
     traffic = committed_traffic()
 
+    tracking_rep = None
+    if extra and args.tracking:
+        tracking_rep = run_tracking_section(itm, torch, dev, stream, scene, raw_dev, poses, ci, depth, vtx, nrm,
+                                            flush, n_pix, H, W, [k for k in idx if k >= 1][:24])
+
     # end to end through the public API with host buffers: pinned u16 frame
     # in, vertex + normal maps out, every step
     e2e = None
@@ -705,6 +772,7 @@ def run_ours(args, world, rank, local):
         "gpu_launches": 6 * args.steps,  # u16, enumerate, commit (+ overflow), visible + range, integrate, raycast
         "batched": batched_rep,
         "learned": learned_rep,
+        "tracking": tracking_rep,
     }
     print(json.dumps(line), flush=True)
 
@@ -719,6 +787,7 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-learned", dest="learned", action="store_false")
+    ap.add_argument("--no-tracking", dest="tracking", action="store_false")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

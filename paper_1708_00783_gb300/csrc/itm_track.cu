@@ -10,9 +10,12 @@
 //    J = (T p x N, N) give J J^T, J r, r^2 and a count.  The per-pixel
 //    arithmetic is float with each operation rounded on its own (built with
 //    -fmad=false), so the selection of pixels is the same on any IEEE
-//    machine; a thread accumulates its few pixels in float, a CTA reduces in
-//    double and writes one partial row.
-//  * icp_solve_kernel (one warp): sums the partial rows in CTA order (the
+//    machine; a thread accumulates its pixels (about eight) in float and a
+//    warp adds its lanes by a float shuffle tree (FP64 is a small fraction
+//    of the FP32 rate here); the CTA adds its warps in double and writes one
+//    partial row.  Each float sum is within 13 roundings of 2^-24 of the
+//    magnitude of its terms.
+//  * icp_solve_kernel (one CTA): sums the partial rows in a fixed order (the
 //    result does not depend on scheduling), then, in double, solves
 //    H x = -g by Cholesky and applies the motion x = (omega, tau) on the world
 //    side, T <- [R(omega) | tau] T with R by Rodrigues' formula.  The pose
@@ -53,7 +56,7 @@ struct IcpState {
 };
 
 // Partial sums of CTA blockIdx.x: partials[b * kIcpSums + k].  The pose is
-// read from T_dev (or T_arg when T_dev is null).
+// read from the tracker state st (or T_arg when st is null).
 __global__ void __launch_bounds__(kIcpThreads) icp_partial_kernel(
     const float *__restrict__ depth, int W, int H, Intr in, const IcpState *__restrict__ st, Mat34 T_arg,
     const float4 *__restrict__ V, const float4 *__restrict__ N, Intr ref, Mat34 M, float dist_thresh,
@@ -72,49 +75,85 @@ __global__ void __launch_bounds__(kIcpThreads) icp_partial_kernel(
     for (int k = 0; k < kIcpSums - 1; ++k) acc[k] = 0.0f;
     int count = 0;
     const int n_pix = W * H;
-    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < n_pix; p += gridDim.x * blockDim.x) {
-        const float d = __ldg(&depth[p]);
-        if (!(d > 0.0f)) continue;
-        const int u = p % W, v = p / W;
-        const float pcx = fmul(fdiv(fsub((float)u, in.cx), in.fx), d);
-        const float pcy = fmul(fdiv(fsub((float)v, in.cy), in.fy), d);
-        float pw[3], pr[3];
+    // kBatch pixels per pass (p, p + stride, ...): their depth loads, then
+    // their map loads, are issued together
+    constexpr int kBatch = 4;
+    const int stride = gridDim.x * blockDim.x;
+    for (int p0 = blockIdx.x * blockDim.x + threadIdx.x; p0 < n_pix; p0 += kBatch * stride) {
+        float dk[kBatch];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) pw[r] = row_apply(T.m + 4 * r, pcx, pcy, d);
+        for (int b = 0; b < kBatch; ++b) {
+            const int p = p0 + b * stride;
+            dk[b] = p < n_pix ? __ldg(&depth[p]) : 0.0f;
+        }
+        float pw[kBatch][3];
+        int o[kBatch];
 #pragma unroll
-        for (int r = 0; r < 3; ++r) pr[r] = row_apply(M.m + 4 * r, pw[0], pw[1], pw[2]);
-        if (!(pr[2] > 0.0f)) continue;
-        const float ur = fadd(fdiv(fmul(ref.fx, pr[0]), pr[2]), ref.cx);
-        const float vr = fadd(fdiv(fmul(ref.fy, pr[1]), pr[2]), ref.cy);
-        if (!(ur >= 0.0f && ur <= (float)(ref.W - 1) && vr >= 0.0f && vr <= (float)(ref.H - 1))) continue;
-        const size_t o = (size_t)(int)fadd(vr, 0.5f) * ref.W + (int)fadd(ur, 0.5f);
-        const float4 Vp = __ldg(&V[o]), Np = __ldg(&N[o]);
-        if (!(Vp.w > 0.0f && Np.w > 0.0f)) continue;
-        const float dx = fsub(pw[0], Vp.x), dy = fsub(pw[1], Vp.y), dz = fsub(pw[2], Vp.z);
-        const float dist2 = fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz));
-        if (!(dist2 <= t2)) continue;
-        const float res = fadd(fadd(fmul(dx, Np.x), fmul(dy, Np.y)), fmul(dz, Np.z));
-        const float J[6] = {fsub(fmul(pw[1], Np.z), fmul(pw[2], Np.y)), fsub(fmul(pw[2], Np.x), fmul(pw[0], Np.z)),
-                            fsub(fmul(pw[0], Np.y), fmul(pw[1], Np.x)), Np.x, Np.y, Np.z};
-        int k = 0;
+        for (int b = 0; b < kBatch; ++b) {
+            o[b] = -1;
+            const float d = dk[b];
+            if (!(d > 0.0f)) continue;
+            const int p = p0 + b * stride;
+            const int u = p % W, v = p / W;
+            const float pcx = fmul(fdiv(fsub((float)u, in.cx), in.fx), d);
+            const float pcy = fmul(fdiv(fsub((float)v, in.cy), in.fy), d);
+            float pr[3];
 #pragma unroll
-        for (int i = 0; i < 6; ++i)
+            for (int r = 0; r < 3; ++r) pw[b][r] = row_apply(T.m + 4 * r, pcx, pcy, d);
 #pragma unroll
-            for (int j = i; j < 6; ++j, ++k) acc[k] = fadd(acc[k], fmul(J[i], J[j]));
+            for (int r = 0; r < 3; ++r) pr[r] = row_apply(M.m + 4 * r, pw[b][0], pw[b][1], pw[b][2]);
+            if (!(pr[2] > 0.0f)) continue;
+            const float ur = fadd(fdiv(fmul(ref.fx, pr[0]), pr[2]), ref.cx);
+            const float vr = fadd(fdiv(fmul(ref.fy, pr[1]), pr[2]), ref.cy);
+            if (!(ur >= 0.0f && ur <= (float)(ref.W - 1) && vr >= 0.0f && vr <= (float)(ref.H - 1))) continue;
+            o[b] = (int)fadd(vr, 0.5f) * ref.W + (int)fadd(ur, 0.5f);
+        }
+        float4 Vk[kBatch], Nk[kBatch];
 #pragma unroll
-        for (int i = 0; i < 6; ++i) acc[21 + i] = fadd(acc[21 + i], fmul(J[i], res));
-        acc[27] = fadd(acc[27], fmul(res, res));
-        ++count;
+        for (int b = 0; b < kBatch; ++b) {
+            Vk[b] = make_float4(0.f, 0.f, 0.f, 0.f);
+            Nk[b] = Vk[b];
+            if (o[b] >= 0) {
+                Vk[b] = __ldg(&V[o[b]]);
+                Nk[b] = __ldg(&N[o[b]]);
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < kBatch; ++b) {
+            if (o[b] < 0) continue;
+            const float4 Vp = Vk[b], Np = Nk[b];
+            if (!(Vp.w > 0.0f && Np.w > 0.0f)) continue;
+            const float dx = fsub(pw[b][0], Vp.x), dy = fsub(pw[b][1], Vp.y), dz = fsub(pw[b][2], Vp.z);
+            const float dist2 = fadd(fadd(fmul(dx, dx), fmul(dy, dy)), fmul(dz, dz));
+            if (!(dist2 <= t2)) continue;
+            const float res = fadd(fadd(fmul(dx, Np.x), fmul(dy, Np.y)), fmul(dz, Np.z));
+            const float J[6] = {fsub(fmul(pw[b][1], Np.z), fmul(pw[b][2], Np.y)),
+                                fsub(fmul(pw[b][2], Np.x), fmul(pw[b][0], Np.z)),
+                                fsub(fmul(pw[b][0], Np.y), fmul(pw[b][1], Np.x)), Np.x, Np.y, Np.z};
+            int k = 0;
+#pragma unroll
+            for (int i = 0; i < 6; ++i)
+#pragma unroll
+                for (int j = i; j < 6; ++j, ++k) acc[k] = fadd(acc[k], fmul(J[i], J[j]));
+#pragma unroll
+            for (int i = 0; i < 6; ++i) acc[21 + i] = fadd(acc[21 + i], fmul(J[i], res));
+            acc[27] = fadd(acc[27], fmul(res, res));
+            ++count;
+        }
     }
-    // CTA reduction in double: warps by shuffles, then warp rows in order
+    // warps by float shuffle trees (the count exactly, as an integer), then
+    // the CTA's warp rows in double, in order
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-    for (int k = 0; k < kIcpSums; ++k) {
-        double x = k < kIcpSums - 1 ? (double)acc[k] : (double)count;
+    for (int k = 0; k < kIcpSums - 1; ++k) {
+        float x = acc[k];
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(kFull, x, off);
-        if (lane == 0) red[warp][k] = x;
+        for (int off = 16; off > 0; off >>= 1) x = fadd(x, __shfl_down_sync(kFull, x, off));
+        if (lane == 0) red[warp][k] = (double)x;
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) count += __shfl_down_sync(kFull, count, off);
+    if (lane == 0) red[warp][kIcpSums - 1] = (double)count;
     __syncthreads();
     if (threadIdx.x < kIcpSums) {
         double x = 0.0;
@@ -124,20 +163,24 @@ __global__ void __launch_bounds__(kIcpThreads) icp_partial_kernel(
     }
 }
 
-// Sums the n_part partial rows in CTA order into sums (lanes split the 29
-// columns); with st, lane 0 then takes the Gauss-Newton step.
-__global__ void __launch_bounds__(32) icp_solve_kernel(const double *__restrict__ partials, int n_part,
-                                                       double *__restrict__ sums, IcpState *st)
+// Sums the n_part partial rows into sums: warp w adds column w, lane l the
+// rows l, l + 32, ... in order, then a fixed shuffle tree (the result does
+// not depend on scheduling); with st, thread 0 then takes the Gauss-Newton
+// step.
+__global__ void __launch_bounds__(1024) icp_solve_kernel(const double *__restrict__ partials, int n_part,
+                                                         double *__restrict__ sums, IcpState *st)
 {
     if (st && st->done) return;
-    const int lane = threadIdx.x;
-    if (lane < kIcpSums) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (warp < kIcpSums) {
         double x = 0.0;
-        for (int b = 0; b < n_part; ++b) x += partials[(size_t)b * kIcpSums + lane];
-        sums[lane] = x;
+        for (int b = lane; b < n_part; b += 32) x += partials[(size_t)b * kIcpSums + warp];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(kFull, x, off);
+        if (lane == 0) sums[warp] = x;
     }
-    __syncwarp();
-    if (!st || lane != 0) return;
+    __syncthreads();
+    if (!st || threadIdx.x != 0) return;
     if (sums[28] < 6.0) {
         st->done = 1;
         return;
@@ -207,9 +250,9 @@ int icp_grid(int n_pix)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (sms < 1) sms = 1;
     }
-    // about two pixels per thread, at most four CTAs per SM and kIcpMaxPartials rows
-    int g = (n_pix + 2 * kIcpThreads - 1) / (2 * kIcpThreads);
-    if (g > 4 * sms) g = 4 * sms;
+    // about eight pixels per thread, at most two CTAs per SM and kIcpMaxPartials rows
+    int g = (n_pix + 8 * kIcpThreads - 1) / (8 * kIcpThreads);
+    if (g > 2 * sms) g = 2 * sms;
     if (g > kIcpMaxPartials) g = kIcpMaxPartials;
     return g > 0 ? g : 1;
 }
@@ -233,7 +276,7 @@ cudaError_t launch_icp_reduce(const float *depth, const Intr &in, const Mat34 &T
     double *partials = work + kIcpSums;
     icp_partial_kernel<<<g, kIcpThreads, 0, st>>>(depth, in.W, in.H, in, nullptr, T_g, V, N, ref, M_ref, dist_thresh,
                                                    partials);
-    icp_solve_kernel<<<1, 32, 0, st>>>(partials, g, work, nullptr);
+    icp_solve_kernel<<<1, 1024, 0, st>>>(partials, g, work, nullptr);
     return cudaGetLastError();
 }
 
@@ -293,7 +336,7 @@ cudaError_t launch_track(const float *depth, const Intr &in0, int levels, const 
         for (int it = 0; it < iters[l]; ++it) {
             icp_partial_kernel<<<g, kIcpThreads, 0, st>>>(lev[l], li[l].W, li[l].H, li[l], state, Mat34{}, V, N, ref,
                                                            M_ref, thresh[l], partials);
-            icp_solve_kernel<<<1, 32, 0, st>>>(partials, g, work, state);
+            icp_solve_kernel<<<1, 1024, 0, st>>>(partials, g, work, state);
         }
     }
     e = cudaMemcpyAsync(&h_state, state, sizeof(h_state), cudaMemcpyDeviceToHost, st);

@@ -3,9 +3,9 @@
 * pyramid level: bit-exact (same float operations);
 * ICP sums: the pixel count is exact (the per-pixel decisions are the same
   float operations on both sides); every other sum within 2e-6 of the sum of
-  its terms' magnitudes (the GPU adds each thread's few products in float,
-  the oracle adds exact products in double: a float rounding of 2^-24 per
-  addition, a handful of additions per thread);
+  its terms' magnitudes (the GPU adds a thread's ~8 products and then a
+  warp's 32 lanes in float, at most 13 roundings of 2^-24 relative to that
+  magnitude; the oracle adds exact products in double);
 * host step: the oracle's step (both in double) to 1e-6;
 * tracking: the oracle's final pose matrix within 1e-5 per element (an
   angle from the trace of R^T R' is no finer than ~0.02 degree for float
