@@ -39,20 +39,40 @@ if ROOT not in sys.path:
 N_FRAMES = 300
 WORKLOAD_NAME = "kinect room 640x480, 5 mm voxels, mu 20 mm, 2^20 buckets + 2^17 excess, 2^19 blocks, 300-frame trajectory"
 METRIC = "frames/s (alloc+fuse+raycast, 640x480 @ 5 mm)"
+# the other configurations of the method, selectable with --workload (the
+# default, kinect, is the one the metric is quoted on):
+# name -> (frames in the trajectory, description, metric)
+WORKLOADS = {
+    "kinect": (N_FRAMES, WORKLOAD_NAME, METRIC),
+    "tiny": (10, "tiny analytic scene 160x120, 10 mm voxels, mu 40 mm, 2^16 buckets + 2^14 excess, 2^16 blocks, "
+                 "10-frame arc (repeated)", "frames/s (alloc+fuse+raycast, 160x120 @ 10 mm)"),
+    "large": (1000, "corridor 20x10x3 m with 200 primitives, 640x480, 2 mm voxels, mu 10 mm, 2^23 buckets + 2^21 "
+                    "excess, 2^23 blocks (21.5 GB of voxels: the walk outgrows 2^21 blocks within 300 frames, and "
+                    "HBM holds it without swapping), 1000-frame walk", "frames/s (alloc+fuse+raycast, 640x480 @ 2 mm)"),
+}
+
+
+def make_workload(name, seed):
+    from synth import kinect_workload, large_workload, tiny_workload
+    if name == "tiny":
+        return tiny_workload(seed=seed)
+    if name == "large":
+        w = large_workload(seed=seed, num_buckets=1 << 23)
+        w.params = dict(w.params, num_excess=1 << 21, num_blocks=1 << 23)
+        return w
+    return kinect_workload(seed=seed)
 L2_FLUSH_BYTES = 256 << 20
 
 
 # ----------------------------------------------------------------- inputs
 
 def _render(args):
-    seed, k = args
-    from synth import kinect_workload
-    w = kinect_workload(seed=seed)
-    f = w.frame(k)
+    seed, k, name = args
+    f = make_workload(name, seed).frame(k)
     return k, f.depth_u16, f.T_wc
 
 
-def render_frames(seed, indices, procs=None):
+def render_frames(seed, indices, procs=None, name="kinect"):
     """Frames of the seeded trajectory, rendered by a spawn pool (started
     before any CUDA call)."""
     procs = procs or min(len(indices), os.cpu_count() or 1, 32)
@@ -60,11 +80,11 @@ def render_frames(seed, indices, procs=None):
     if procs > 1 and len(indices) > 4:
         ctx = mp.get_context("spawn")
         with ctx.Pool(procs) as pool:
-            for k, d, T in pool.imap_unordered(_render, [(seed, k) for k in indices], chunksize=4):
+            for k, d, T in pool.imap_unordered(_render, [(seed, k, name) for k in indices], chunksize=4):
                 out[k] = (d, T)
     else:
         for k in indices:
-            _, d, T = _render((seed, k))
+            _, d, T = _render((seed, k, name))
             out[k] = (d, T)
     return out
 
@@ -237,17 +257,16 @@ def sum_over_ranks(value, world, device=None):
 
 # ----------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_sample(frames, stride=30, budget_s=30.0):
+def cpu_oracle_sample(frames, stride=30, budget_s=30.0, name="kinect"):
     """The oracle as it stands, single-threaded, on every `stride`-th frame of
     the trajectory from an empty volume (alloc + integrate + raycast each),
     stopping once `budget_s` of work is done."""
     import oracle
-    from synth import kinect_workload
-    w = kinect_workload()
+    w = make_workload(name, 0)
     sc = oracle.Scene(**w.params)
     ia = w.intr.as_array()
     done, t0, upd = 0, time.perf_counter(), 0
-    idx = list(range(0, N_FRAMES, stride))
+    idx = sorted(frames)
     for k in idx:
         raw, T = frames[k]
         d = oracle.depth_u16_to_f32(raw)
@@ -259,9 +278,9 @@ def cpu_oracle_sample(frames, stride=30, budget_s=30.0):
             break
     dt = time.perf_counter() - t0
     return {"value": done / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": "%d frames (every %dth of the 300-frame trajectory from frame 0, empty volume at start), "
+            "sample": "%d frames (every %dth of the %d-frame trajectory from frame 0, empty volume at start), "
                       "u16->f32 + allocate + integrate over all allocated blocks + raycast, single thread"
-                      % (done, stride),
+                      % (done, stride, WORKLOADS[name][0]),
             "voxel_updates_per_s": upd / dt, "seconds": dt}
 
 
@@ -586,11 +605,15 @@ def _rms_pair(w, const, learned_):
 def run_ours(args, world, rank, local):
     # render before the first CUDA call (spawn pool)
     seed = rank
+    n_frames, workload_desc, metric = WORKLOADS[args.workload]
     total_frames = args.warmup + args.steps
-    idx = sorted({k % N_FRAMES for k in range(total_frames)})
-    frames = render_frames(seed, idx)
-    cpu_frames = render_frames(0, list(range(0, N_FRAMES, 30))) if (rank == 0 and world == 1 and args.cpu_baseline) else None
-    extra = rank == 0 and world == 1
+    idx = sorted({k % n_frames for k in range(total_frames)})
+    frames = render_frames(seed, idx, name=args.workload)
+    cpu_stride = max(1, n_frames // 10)
+    cpu_frames = (render_frames(0, list(range(0, n_frames, cpu_stride)), name=args.workload)
+                  if (rank == 0 and world == 1 and args.cpu_baseline) else None)
+    # the batched, learned and tracking sections belong to the room workload
+    extra = rank == 0 and world == 1 and args.workload == "kinect"
     n_bsteps = 20
     if extra and args.batched:
         main_b = render_frames(0, list(range(n_bsteps)))
@@ -604,9 +627,8 @@ def run_ours(args, world, rank, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import paper_1708_00783_gb300 as itm
-    from synth import kinect_workload
 
-    w = kinect_workload(seed=seed)
+    w = make_workload(args.workload, seed)
     H, W = w.intr.height, w.intr.width
     ci = itm.make_intrinsics(W, H, w.intr.fx, w.intr.fy, w.intr.cx, w.intr.cy)
     dev = torch.device("cuda", local)
@@ -628,7 +650,7 @@ def run_ours(args, world, rank, local):
         itm.itm_raycast(scene.handle, ci, poses[k], vtx, nrm, stream)
 
     for i in range(args.warmup):
-        step(i % N_FRAMES)
+        step(i % n_frames)
     torch.cuda.synchronize()
     st0 = scene.stats()
 
@@ -638,7 +660,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.synchronize()
     with ClockSampler(local) as clk:
         for i in range(args.steps):
-            k = (args.warmup + i) % N_FRAMES
+            k = (args.warmup + i) % n_frames
             e = ev[i]
             e[0].record(stream)
             itm.itm_depth_u16_to_f32(raw_dev[k], depth, n_pix, stream)
@@ -674,7 +696,7 @@ def run_ours(args, world, rank, local):
     alg_bytes = 10.0 * updated + 4.0 * n_pix * args.steps + 12.0 * visible_blocks
     achieved = alg_bytes / (integ_ms / 1000.0) / 1e9
     peak, peak_kind = load_peaks()
-    traffic = committed_traffic()
+    traffic = committed_traffic() if args.workload == "kinect" else None  # captured on the room workload
 
     tracking_rep = None
     if extra and args.tracking:
@@ -699,14 +721,14 @@ def run_ours(args, world, rank, local):
             host_n.copy_(nrm, non_blocking=True)
 
         for i in range(args.warmup):
-            e2e_step(i % N_FRAMES)
+            e2e_step(i % n_frames)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
         for i in range(args.steps):
-            e2e_step((args.warmup + i) % N_FRAMES)
+            e2e_step((args.warmup + i) % n_frames)
         b.record(stream)
         torch.cuda.synchronize()
         e_ms = max_over_ranks(a.elapsed_time(b), world, dev)
@@ -721,14 +743,14 @@ def run_ours(args, world, rank, local):
 
     cpu = None
     if cpu_frames is not None:
-        cpu = cpu_oracle_sample(cpu_frames)
+        cpu = cpu_oracle_sample(cpu_frames, stride=cpu_stride, name=args.workload)
         cpu = {k: v for k, v in cpu.items() if k != "seconds"}
 
     if rank != 0:
         return
     clocks = clk.summary()
     line = {
-        "metric": METRIC,
+        "metric": metric,
         "value": fps,
         "unit": "frames/s",
         "n_gpus": world,
@@ -741,9 +763,9 @@ def run_ours(args, world, rank, local):
         "dtype": "f32",
         "data": "synthetic",
         "config": {
-            "workload": WORKLOAD_NAME,
-            "frames": "warm-up frames 0..%d, timed frames %d..%d (mod 300)" % (args.warmup - 1, args.warmup,
-                                                                              args.warmup + args.steps - 1),
+            "workload": workload_desc,
+            "frames": "warm-up frames 0..%d, timed frames %d..%d (mod %d)" % (args.warmup - 1, args.warmup,
+                                                                             args.warmup + args.steps - 1, n_frames),
             "input": "uint16 millimetre depth resident in HBM, converted on the device each step",
             "l2": "flushed between steps (256 MB write, outside the timed events)",
             "parallelism": "independent trajectory per rank" if world > 1 else "single GPU",
@@ -788,6 +810,9 @@ def main(argv=None):
     ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--no-learned", dest="learned", action="store_false")
     ap.add_argument("--no-tracking", dest="tracking", action="store_false")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="kinect",
+                    help="configuration of the per-frame loop (default: the 640x480 / 5 mm room the metric is "
+                         "quoted on); the batched, learned and tracking sections run with the default only")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
