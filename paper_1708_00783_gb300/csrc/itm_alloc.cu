@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) build_visible_range_kernel(SceneDev s, Ma
     }
 }
 
-int persistent_grid(int threads, const void *kernel)
+int sm_count()
 {
     static int cached_sm = 0;
     if (!cached_sm) {
@@ -101,10 +101,15 @@ int persistent_grid(int threads, const void *kernel)
         cudaDeviceGetAttribute(&cached_sm, cudaDevAttrMultiProcessorCount, dev);
         if (cached_sm <= 0) cached_sm = 1;
     }
+    return cached_sm;
+}
+
+int persistent_grid(int threads, const void *kernel)
+{
     int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
     if (per_sm < 1) per_sm = 1;
-    return cached_sm * per_sm;
+    return sm_count() * per_sm;
 }
 
 }  // namespace
@@ -120,7 +125,9 @@ cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &i
     const int n_range_tiles = with_range ? ((in.W + 7) / 8) * ((in.H + 3) / 4) : 0;
     alloc_enumerate_kernel<<<grid, 256, 0, st>>>(s, depth, in, T_wc, inv_b, n_range_tiles);
     static int g_commit = 0, g_visible = 0, g_visrange = 0;
-    if (!g_commit) g_commit = persistent_grid(256, (const void *)alloc_commit_kernel);
+    // one CTA per SM: a frame's requests (usually a few thousand) fit in one
+    // pass, and fewer CTAs pay the completion count's fences
+    if (!g_commit) g_commit = sm_count();
     if (!g_visible) g_visible = persistent_grid(256, (const void *)build_visible_kernel);
     if (!g_visrange) g_visrange = persistent_grid(256, (const void *)build_visible_range_kernel);
     alloc_commit_kernel<<<g_commit, 256, 0, st>>>(s);
