@@ -100,6 +100,10 @@ def _load():
     lib.orc_icp_update.restype = I
     lib.orc_icp_update.argtypes = [f64p, f32p, P]
     i32p_ = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+    lib.orc_mesh.restype = ctypes.c_longlong
+    lib.orc_mesh.argtypes = [P, P, ctypes.c_longlong]
+    lib.orc_cell_triangles.restype = I
+    lib.orc_cell_triangles.argtypes = [f32p, i32p_]
     lib.orc_track.restype = I
     lib.orc_track.argtypes = [f32p, I, I, f32p, I, i32p_, f32p, f32p, f32p, I, I, f32p, f32p, f32p]
     _lib = lib
@@ -195,6 +199,14 @@ class Scene:
         out = np.zeros((nb + ne, 5), dtype=np.int32)
         _load().orc_entries(self.p, out)
         return out
+
+    def mesh(self):
+        """Marching-Cubes triangles of the zero level set: float32 [n, 3, 3]
+        (three world-space vertices each, counter-clockwise seen from F > 0)."""
+        n = int(_load().orc_mesh(self.p, None, 0))
+        out = np.zeros((max(n, 1), 3, 3), dtype=np.float32)
+        _load().orc_mesh(self.p, out.ctypes.data, n)
+        return out[:n]
 
     def set_block(self, b, sdf, w):
         """Allocate block b (if missing) and set its 512 voxels (x + 8y + 64z)."""
@@ -327,3 +339,11 @@ def track(depth, intr, iters, thresh, V, N, intr_r, T_ref, T_init):
     steps = _load().orc_track(d, W, H, _f32(intr), len(it), it, _f32(thresh), V.ravel(), N.ravel(), Wr, Hr,
                               _f32(intr_r), _f32(T_ref).ravel(), T)
     return T.reshape(4, 4), int(steps)
+
+
+def cell_triangles(F):
+    """Marching-Cubes triangles of one cell with corner values F[8] (corner
+    k at (k & 1, (k >> 1) & 1, k >> 2)), as edge indices [n, 3]."""
+    tri = np.zeros(36, dtype=np.int32)
+    n = _load().orc_cell_triangles(_f32(F), tri)
+    return tri[:3 * n].reshape(n, 3)

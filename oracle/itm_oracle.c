@@ -25,6 +25,7 @@
  *                         with the Sec. 4.4 state machine
  *   orc_icp_reduce/track  Sec. 4.1.1 depth tracker: point-to-plane sums over
  *                         the raycast maps, Gauss-Newton steps, pyramid
+ *   orc_mesh              Sec. 4 Marching Cubes over the allocated blocks
  *   orc_depth_u16_to_f32  Sec. 4 (ViewBuilder: unsigned short -> float depth)
  *
  * Readings taken where the paper is silent (each one is also listed in the
@@ -989,6 +990,179 @@ int orc_track(const float *depth, int W, int H, const float intr[4], int L, cons
     for (int l = 1; l < L; ++l) free(lev[l]);
     return steps;
 }
+
+/* ----------------------------------------------------------------- meshing */
+
+/*
+ * Marching Cubes (Sec. 4: "mesh generation via the Marching-Cubes
+ * algorithm", Lorensen & Cline 1987) over the zero level set of the TSDF.
+ * The triangulation of a cell is derived here from first principles at run
+ * time, without a case table: on each of the cube's six faces the crossing
+ * points of its sign-changing edges are joined into directed segments (the
+ * inside, F < 0, on the segment's left seen from outside the cube); a face
+ * with four crossings (diagonal corners inside) joins each crossing to the
+ * one across the nearer inside corner, i.e. the inside corners are kept
+ * apart.  That choice depends only on the face's four values, so two cells
+ * sharing a face agree and the mesh is closed.  The segments chain into
+ * closed loops around the cube, each fanned into triangles from its first
+ * point, counter-clockwise seen from the outside (F > 0).
+ *
+ * Corner k of the cell at voxel g sits at g + (k & 1, (k >> 1) & 1, k >> 2).
+ * The crossing on the edge from corner a to corner b (b = a + one axis step)
+ * is at t = F_a / (F_a - F_b) along that axis: position ((float)g_axis + t) * s
+ * on that axis and (float)g * s on the others.
+ */
+
+/* the cube's faces: four corners in counter-clockwise order seen from
+ * outside (outward normals -x, +x, -y, +y, -z, +z) */
+static const int FACE_CORNERS[6][4] = {
+    {0, 4, 6, 2}, {1, 3, 7, 5}, {0, 1, 5, 4}, {2, 6, 7, 3}, {0, 2, 3, 1}, {4, 5, 7, 6},
+};
+
+/* index 0..11 of the edge between corners a and b (differing in one bit) */
+static int edge_index(int a, int b)
+{
+    int lo = a < b ? a : b, hi = a < b ? b : a;
+    int axis = (hi - lo) == 1 ? 0 : (hi - lo) == 2 ? 1 : 2;
+    /* the 4 edges along an axis are indexed by the other two bits of lo */
+    int o1, o2;
+    if (axis == 0) {
+        o1 = (lo >> 1) & 1;
+        o2 = (lo >> 2) & 1;
+    } else if (axis == 1) {
+        o1 = lo & 1;
+        o2 = (lo >> 2) & 1;
+    } else {
+        o1 = lo & 1;
+        o2 = (lo >> 1) & 1;
+    }
+    return 4 * axis + o1 + 2 * o2;
+}
+
+/* Triangles of one cell with corner values F[8] (inside: F < 0); tri
+ * receives edge indices, 3 per triangle.  Returns the triangle count. */
+static int cell_triangles(const float F[8], int *tri)
+{
+    int seg_from[12], seg_to[12], n_seg = 0;
+    for (int f = 0; f < 6; ++f) {
+        const int *q = FACE_CORNERS[f];
+        int A[2], B[2], nA = 0, nB = 0, posA[2], posB[2];
+        for (int i = 0; i < 4; ++i) {
+            int a = q[i], b = q[(i + 1) & 3];
+            int ia = F[a] < 0.0f, ib = F[b] < 0.0f;
+            if (ia == ib) continue;
+            if (ia) { /* inside -> outside along the counter-clockwise walk */
+                posA[nA] = i;
+                A[nA++] = edge_index(a, b);
+            } else {
+                posB[nB] = i;
+                B[nB++] = edge_index(a, b);
+            }
+        }
+        if (nA == 1) {
+            seg_from[n_seg] = A[0];
+            seg_to[n_seg++] = B[0];
+        } else if (nA == 2) {
+            /* diagonal inside corners: the exit crossing on edge i goes to the
+             * entry crossing on edge i - 1, around the inside corner q[i] */
+            for (int k = 0; k < 2; ++k) {
+                int want = (posA[k] + 3) & 3;
+                int j = posB[0] == want ? 0 : 1;
+                seg_from[n_seg] = A[k];
+                seg_to[n_seg++] = B[j];
+            }
+        }
+    }
+    int used[12] = {0}, n_tri = 0;
+    for (int s0 = 0; s0 < n_seg; ++s0) {
+        if (used[s0]) continue;
+        int loop[12], n = 0, cur = s0;
+        for (int guard = 0; guard < 12; ++guard) {
+            used[cur] = 1;
+            loop[n++] = seg_from[cur];
+            int next = -1;
+            for (int t = 0; t < n_seg; ++t)
+                if (!used[t] && seg_from[t] == seg_to[cur]) next = t;
+            if (next < 0) break;
+            cur = next;
+        }
+        /* the loop runs clockwise seen from outside the surface (F > 0):
+         * fan it the other way so the triangles face the outside */
+        for (int i = 1; i + 1 < n; ++i) {
+            tri[3 * n_tri] = loop[0];
+            tri[3 * n_tri + 1] = loop[i + 1];
+            tri[3 * n_tri + 2] = loop[i];
+            ++n_tri;
+        }
+    }
+    return n_tri;
+}
+
+static void edge_corners(int e, int *a, int *b)
+{
+    int axis = e / 4, o = e % 4;
+    int o1 = o & 1, o2 = o >> 1;
+    int lo;
+    if (axis == 0) lo = (o1 << 1) | (o2 << 2);
+    else if (axis == 1) lo = o1 | (o2 << 2);
+    else lo = o1 | (o2 << 1);
+    *a = lo;
+    *b = lo | (1 << axis);
+}
+
+/* Observed value of voxel g, or 0 when unallocated or never observed. */
+static int observed_value(const orc_scene *s, int gx, int gy, int gz, float *F)
+{
+    int ptr = lookup(s, gx >> 3, gy >> 3, gz >> 3);
+    if (ptr < 0) return 0;
+    size_t i = (size_t)ptr * ORC_BLOCK3 + (gx & 7) + 8 * (gy & 7) + 64 * (gz & 7);
+    if (!(s->w[i] > 0.0f)) return 0;
+    *F = s->sdf[i];
+    return 1;
+}
+
+/* Mesh of the scene: every cell whose 8 corner voxels are allocated and
+ * observed, cells visited block by block in allocation order.  Writes up to
+ * cap triangles (9 floats each: three world-space vertices) and returns the
+ * total count. */
+long long orc_mesh(const orc_scene *s, float *out, long long cap)
+{
+    const float vs = s->voxel_size;
+    long long n = 0;
+    for (int b = 0; b < s->n_alloc; ++b) {
+        int ptr = s->alloc_order[b];
+        int bx = s->block_pos[3 * ptr], by = s->block_pos[3 * ptr + 1], bz = s->block_pos[3 * ptr + 2];
+        for (int l = 0; l < ORC_BLOCK3; ++l) {
+            int g[3] = {8 * bx + (l & 7), 8 * by + ((l >> 3) & 7), 8 * bz + (l >> 6)};
+            float F[8];
+            int ok = 1;
+            for (int k = 0; k < 8 && ok; ++k)
+                ok = observed_value(s, g[0] + (k & 1), g[1] + ((k >> 1) & 1), g[2] + (k >> 2), &F[k]);
+            if (!ok) continue;
+            int tri[36];
+            int nt = cell_triangles(F, tri);
+            for (int t = 0; t < nt; ++t, ++n) {
+                if (n >= cap) continue;
+                for (int v = 0; v < 3; ++v) {
+                    int a, c;
+                    edge_corners(tri[3 * t + v], &a, &c);
+                    int axis = (c - a) == 1 ? 0 : (c - a) == 2 ? 1 : 2;
+                    float tt = F[a] / (F[a] - F[c]);
+                    for (int k = 0; k < 3; ++k) {
+                        float coord = (float)(g[k] + ((a >> k) & 1));
+                        if (k == axis) coord = coord + tt;
+                        out[9 * n + 3 * v + k] = coord * vs;
+                    }
+                }
+            }
+        }
+    }
+    return n;
+}
+
+/* Triangles (as edge indices) of a single cell with corner values F[8]:
+ * for tests of the triangulation itself.  tri: int[36].  Returns the count. */
+int orc_cell_triangles(const float *F, int *tri) { return cell_triangles(F, tri); }
 
 /* ---------------------------------------------------------- introspection */
 
