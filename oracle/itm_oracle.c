@@ -1004,8 +1004,10 @@ int orc_track(const float *depth, int W, int H, const float intr[4], int L, cons
  * one across the nearer inside corner, i.e. the inside corners are kept
  * apart.  That choice depends only on the face's four values, so two cells
  * sharing a face agree and the mesh is closed.  The segments chain into
- * closed loops around the cube, each fanned into triangles from its first
- * point, counter-clockwise seen from the outside (F > 0).
+ * closed loops around the cube, each fanned into triangles from its crossing
+ * on the lowest-numbered edge, counter-clockwise seen from the outside
+ * (F > 0).  Edge 4 a + o1 + 2 o2 runs along axis a from the corner whose
+ * other two coordinates are o1 (the lower axis) and o2 (the higher).
  *
  * Corner k of the cell at voxel g sits at g + (k & 1, (k >> 1) & 1, k >> 2).
  * The crossing on the edge from corner a to corner b (b = a + one axis step)
@@ -1086,6 +1088,14 @@ static int cell_triangles(const float F[8], int *tri)
             if (next < 0) break;
             cur = next;
         }
+        /* fan from the crossing on the lowest-numbered edge (a rule that
+         * does not depend on how the loop was found) */
+        int first = 0;
+        for (int i = 1; i < n; ++i)
+            if (loop[i] < loop[first]) first = i;
+        int rot[12];
+        for (int i = 0; i < n; ++i) rot[i] = loop[(first + i) % n];
+        for (int i = 0; i < n; ++i) loop[i] = rot[i];
         /* the loop runs clockwise seen from outside the surface (F > 0):
          * fan it the other way so the triangles face the outside */
         for (int i = 1; i + 1 < n; ++i) {
