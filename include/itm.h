@@ -261,6 +261,22 @@ int itm_track_depth(const float *depth_dev, const itm_intrinsics *intr, int leve
                     const itm_intrinsics *ref_intr, const float T_ref[16], float T_inout[16], int *steps_out,
                     void *scratch_dev, itm_stream stream);
 
+/* Sec. 4 mesh generation by Marching Cubes (Lorensen & Cline 1987): the
+ * zero level set of the TSDF (inside: F < 0) over every cell g + {0,1}^3
+ * whose eight corner voxels are allocated and observed (weight > 0).  The
+ * triangulation of each corner pattern comes from walking the cube's faces
+ * (a face with two diagonal inside corners cuts off each of them, so cells
+ * sharing a face agree and the mesh is closed); each crossing loop is fanned
+ * from its crossing on the lowest-numbered edge, triangles counter-clockwise
+ * seen from outside (F > 0).  A vertex on the edge from voxel g_a to g_b
+ * (one axis step up) sits at (g_a + t) s along that axis, t = F_a / (F_a -
+ * F_b).  triangles_dev: device float[capacity][9] (three world-space
+ * vertices per triangle; order of triangles unspecified), may be NULL when
+ * capacity is 0.  *n_out (host): the number of triangles in the mesh.
+ * Returns ITM_ERR_TOO_LARGE when that exceeds capacity (capacity of them
+ * are written).  Synchronises the stream. */
+int itm_mesh(itm_scene *scene, float *triangles_dev, int64_t capacity, int64_t *n_out, itm_stream stream);
+
 /* One frame of the per-frame core: itm_allocate, itm_integrate and (when
  * vertex_dev is not NULL) itm_raycast, on one stream. */
 int itm_process_frame(itm_scene *scene, const float *depth_dev, const itm_intrinsics *intr,

@@ -21,7 +21,9 @@ LIB_PATH = _build_mod.LIB
 
 ITM_OK = 0
 ERRORS = {1: "ITM_ERR_ARG", 2: "ITM_ERR_CUDA", 3: "ITM_ERR_HASH_FULL", 4: "ITM_ERR_VBA_FULL",
-          5: "ITM_ERR_RANGE", 6: "ITM_ERR_TIMEOUT", 7: "ITM_ERR_OVERFLOW", 8: "ITM_ERR_TOO_LARGE"}
+          5: "ITM_ERR_RANGE", 6: "ITM_ERR_TIMEOUT", 7: "ITM_ERR_OVERFLOW", 8: "ITM_ERR_TOO_LARGE",
+          9: "ITM_ERR_SINGULAR"}
+ITM_ERR_TOO_LARGE = 8
 ITM_NOALLOC_MAX_BLOCKS = 1 << 21
 ITM_MLP_FEATURES, ITM_MLP_HIDDEN, ITM_MLP_PARAMS = 52, 64, 7617
 ITM_MLP_PACKED_BYTES, ITM_MLP_SCRATCH_PER_SAMPLE = 17168, 257
@@ -106,6 +108,7 @@ def _load():
         "itm_raycast_range": (I, [P, ip, fp16, P, P, P]),
         "itm_raycast_combined": (I, [ctypes.POINTER(P), fp16, I, ip, fp16, P, P, P]),
         "itm_depth_halve": (I, [P, I, I, P, P]),
+        "itm_mesh": (I, [P, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), P]),
         "itm_icp_reduce": (I, [P, ip, fp16, P, P, ip, fp16, F, P, P]),
         "itm_icp_step": (I, [ctypes.POINTER(ctypes.c_double), fp16, ctypes.POINTER(ctypes.c_double)]),
         "itm_track_scratch_bytes": (ctypes.c_size_t, [I, I, I]),
@@ -234,6 +237,18 @@ def itm_raycast_combined(scenes, submap_from_world, intr, T_wc, vertex, normal, 
     a, p = _pose(T_wc)
     _check(_lib.itm_raycast_combined(arr, P.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), n, ctypes.byref(intr), p,
                                      _ptr(vertex), _ptr(normal), _stream(stream)), "itm_raycast_combined")
+
+
+def itm_mesh(scene, triangles=None, capacity=0, stream=None):
+    """Marching-Cubes mesh into triangles (device float [capacity, 9]);
+    returns the mesh's triangle count (raises ItmError(ITM_ERR_TOO_LARGE)
+    when it exceeds capacity; use capacity 0 to count)."""
+    n = ctypes.c_int64(0)
+    r = _lib.itm_mesh(scene, _ptr(triangles), int(capacity), ctypes.byref(n), _stream(stream))
+    if r == ITM_ERR_TOO_LARGE and capacity == 0:
+        return n.value
+    _check(r, "itm_mesh")
+    return n.value
 
 
 def itm_depth_halve(depth_in, width, height, depth_out, stream=None):

@@ -38,6 +38,7 @@ SOURCES = {
     "itm_batch.cu": ["-fmad=false"],
     "itm_combined.cu": ["-fmad=false"],
     "itm_track.cu": ["-fmad=false"],
+    "itm_mesh.cu": ["-fmad=false"],
 }
 
 

@@ -59,6 +59,7 @@ struct Counters {
     unsigned long long updated;  // cumulative voxel updates
     unsigned long long visited;  // cumulative voxels visited by integration
     unsigned long long frames;   // cumulative integrated frames
+    unsigned long long mesh_tris;  // per-mesh: triangles found
 };
 
 // Offset and size of the per-frame counters cleared at the start of allocation.
@@ -235,6 +236,7 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
 cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 &M_d, uint32_t *rmin, uint32_t *rmax,
                                  cudaStream_t st);
 bool range_fits(const Intr &in);
+cudaError_t launch_mesh(const SceneDev &s, float *out, long long cap, unsigned long long *counter, cudaStream_t st);
 cudaError_t launch_depth_halve(const float *in, int W, int H, float *out, cudaStream_t st);
 cudaError_t launch_icp_reduce(const float *depth, const Intr &in, const Mat34 &T_g, const float4 *V, const float4 *N,
                               const Intr &ref, const Mat34 &M_ref, float dist_thresh, double *work, cudaStream_t st);

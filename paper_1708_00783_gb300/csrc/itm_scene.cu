@@ -407,6 +407,22 @@ int itm_track_depth(const float *depth_dev, const itm_intrinsics *intr, int leve
     return r;
 }
 
+int itm_mesh(itm_scene *sc, float *triangles_dev, int64_t capacity, int64_t *n_out, itm_stream stream)
+{
+    if (!sc || capacity < 0 || (capacity > 0 && !triangles_dev) || !n_out) return ITM_ERR_ARG;
+    if (reinterpret_cast<uintptr_t>(triangles_dev) & 3) return ITM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    sc->last_stream = st;
+    unsigned long long *counter = &sc->d.ctr->mesh_tris;
+    cudaError_t e = launch_mesh(sc->d, triangles_dev, (long long)capacity, counter, st);
+    unsigned long long cnt = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&cnt, counter, sizeof(cnt), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return check_cuda(e);
+    *n_out = (int64_t)cnt;
+    return (int64_t)cnt > capacity ? ITM_ERR_TOO_LARGE : ITM_OK;
+}
+
 int itm_process_frame(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
                       float *vertex_dev, float *normal_dev, itm_stream stream)
 {
