@@ -9,6 +9,17 @@
 
 #include "itm_internal.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// An NVTX range named after the C-ABI call for the duration of the call, so
+// profiler timelines group each call's kernels (no cost without a profiler).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+}  // namespace
+
 namespace itm {
 
 int overflow_capacity();  // itm_alloc.cu
@@ -171,6 +182,7 @@ int itm_scene_destroy(itm_scene *sc)
 
 int itm_scene_reset(itm_scene *sc, itm_stream stream)
 {
+    Range range_("itm_scene_reset");
     if (!sc) return ITM_ERR_ARG;
     sc->alloc_epoch++;
     cudaStream_t st = (cudaStream_t)stream;
@@ -181,6 +193,7 @@ int itm_scene_reset(itm_scene *sc, itm_stream stream)
 int itm_allocate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
                  itm_stream stream)
 {
+    Range range_("itm_allocate");
     if (!sc || !depth_dev || !valid_pose(T_wc) || !valid_intr(intr)) return ITM_ERR_ARG;
     Mat34 T, M;
     pose_rows(T_wc, T);
@@ -203,6 +216,7 @@ int itm_allocate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *in
 int itm_integrate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
                   itm_stream stream)
 {
+    Range range_("itm_integrate");
     if (!sc || !depth_dev || !valid_pose(T_wc) || !valid_intr(intr)) return ITM_ERR_ARG;
     if (sc->d.weight_mode != 0) return ITM_ERR_ARG;
     Mat34 M;
@@ -215,6 +229,7 @@ int itm_integrate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *i
 int itm_integrate_weighted(itm_scene *sc, const float *depth_dev, const float *wpx_dev, const itm_intrinsics *intr,
                            const float T_wc[16], itm_stream stream)
 {
+    Range range_("itm_integrate_weighted");
     if (!sc || !depth_dev || !wpx_dev || !valid_pose(T_wc) || !valid_intr(intr)) return ITM_ERR_ARG;
     if (sc->d.weight_mode != 1) return ITM_ERR_ARG;
     Mat34 M;
@@ -227,6 +242,7 @@ int itm_integrate_weighted(itm_scene *sc, const float *depth_dev, const float *w
 int itm_raycast(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16], float *vertex_dev,
                 float *normal_dev, itm_stream stream)
 {
+    Range range_("itm_raycast");
     if (!sc || !valid_pose(T_wc) || !vertex_dev || !normal_dev || !valid_intr(intr)) return ITM_ERR_ARG;
     if ((reinterpret_cast<uintptr_t>(vertex_dev) & 15) || (reinterpret_cast<uintptr_t>(normal_dev) & 15))
         return ITM_ERR_ARG;
@@ -250,6 +266,7 @@ int itm_raycast(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16],
 int itm_raycast_range(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16], float *zmin_dev,
                       float *zmax_dev, itm_stream stream)
 {
+    Range range_("itm_raycast_range");
     if (!sc || !valid_pose(T_wc) || !zmin_dev || !zmax_dev || !valid_intr(intr)) return ITM_ERR_ARG;
     if (zmin_dev == reinterpret_cast<float *>(sc->d.range_min) || zmax_dev == reinterpret_cast<float *>(sc->d.range_max))
         return ITM_ERR_ARG;
@@ -265,6 +282,7 @@ int itm_raycast_combined(itm_scene *const *scenes, const float *submap_from_worl
                          const itm_intrinsics *intr, const float T_wc[16], float *vertex_dev, float *normal_dev,
                          itm_stream stream)
 {
+    Range range_("itm_raycast_combined");
     if (!scenes || !submap_from_world || n < 1 || n > ITM_COMBINED_MAX || !valid_intr(intr) || !valid_pose(T_wc) ||
         !vertex_dev || !normal_dev)
         return ITM_ERR_ARG;
@@ -293,6 +311,7 @@ int itm_raycast_combined(itm_scene *const *scenes, const float *submap_from_worl
 
 int itm_depth_halve(const float *in_dev, int width, int height, float *out_dev, itm_stream stream)
 {
+    Range range_("itm_depth_halve");
     if (!in_dev || !out_dev || width < 2 || height < 2 || (long long)width * height >= (1ll << 30)) return ITM_ERR_ARG;
     return check_cuda(launch_depth_halve(in_dev, width, height, out_dev, (cudaStream_t)stream));
 }
@@ -303,6 +322,7 @@ int itm_icp_reduce(const float *depth_dev, const itm_intrinsics *intr, const flo
                    const float *normal_dev, const itm_intrinsics *ref_intr, const float T_ref[16], float dist_thresh,
                    double *work_dev, itm_stream stream)
 {
+    Range range_("itm_icp_reduce");
     if (!depth_dev || !valid_intr(intr) || !valid_pose(T_g) || !vertex_dev || !normal_dev || !valid_intr(ref_intr) ||
         !valid_pose(T_ref) || !valid_thresh(dist_thresh) || !work_dev)
         return ITM_ERR_ARG;
@@ -387,6 +407,7 @@ int itm_track_depth(const float *depth_dev, const itm_intrinsics *intr, int leve
                     const itm_intrinsics *ref_intr, const float T_ref[16], float T_inout[16], int *steps_out,
                     void *scratch_dev, itm_stream stream)
 {
+    Range range_("itm_track_depth");
     if (!depth_dev || !valid_intr(intr) || levels < 1 || levels > ITM_TRACK_MAX_LEVELS || !iters || !dist_thresh ||
         !vertex_dev || !normal_dev || !valid_intr(ref_intr) || !valid_pose(T_ref) || !T_inout ||
         !valid_pose(T_inout) || !scratch_dev)
@@ -409,6 +430,7 @@ int itm_track_depth(const float *depth_dev, const itm_intrinsics *intr, int leve
 
 int itm_mesh(itm_scene *sc, float *triangles_dev, int64_t capacity, int64_t *n_out, itm_stream stream)
 {
+    Range range_("itm_mesh");
     if (!sc || capacity < 0 || (capacity > 0 && !triangles_dev) || !n_out) return ITM_ERR_ARG;
     if (reinterpret_cast<uintptr_t>(triangles_dev) & 3) return ITM_ERR_ARG;
     cudaStream_t st = (cudaStream_t)stream;
@@ -426,6 +448,7 @@ int itm_mesh(itm_scene *sc, float *triangles_dev, int64_t capacity, int64_t *n_o
 int itm_process_frame(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
                       float *vertex_dev, float *normal_dev, itm_stream stream)
 {
+    Range range_("itm_process_frame");
     if (!sc || (vertex_dev && !normal_dev)) return ITM_ERR_ARG;
     int r = itm_allocate(sc, depth_dev, intr, T_wc, stream);
     if (r == ITM_OK) r = itm_integrate(sc, depth_dev, intr, T_wc, stream);
@@ -435,6 +458,7 @@ int itm_process_frame(itm_scene *sc, const float *depth_dev, const itm_intrinsic
 
 int itm_depth_u16_to_f32(const uint16_t *raw_dev, float *depth_dev, int64_t n, itm_stream stream)
 {
+    Range range_("itm_depth_u16_to_f32");
     if (n < 0 || (n > 0 && (!raw_dev || !depth_dev))) return ITM_ERR_ARG;
     return check_cuda(launch_depth_u16(raw_dev, depth_dev, n, (cudaStream_t)stream));
 }
@@ -476,6 +500,7 @@ int itm_scene_status(itm_scene *sc)
 // at reset the list is the identity, so they are block indices 0 .. n-1.
 int itm_scene_export(itm_scene *sc, int16_t *coords_host, float *sdf_host, float *w_host, int cap, int *n)
 {
+    Range range_("itm_scene_export");
     if (!sc || !n || cap < 0 || (cap > 0 && !coords_host)) return ITM_ERR_ARG;
     itm_stats st;
     int r = itm_scene_stats(sc, &st);
@@ -554,6 +579,7 @@ int itm_scene_export_table(itm_scene *sc, int32_t *entries_host)
 
 int itm_scene_import(itm_scene *sc, const int16_t *coords_host, const float *sdf_host, const float *w_host, int n)
 {
+    Range range_("itm_scene_import");
     if (!sc || n < 0 || n > sc->d.nv || (n > 0 && (!coords_host || !sdf_host || !w_host))) return ITM_ERR_ARG;
     const SceneDev &d = sc->d;
     // Sec. 3.3 insertion, sequentially on the host: bucket first, then the
