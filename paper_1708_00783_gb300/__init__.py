@@ -17,12 +17,14 @@ import numpy as np
 from . import build as _build_mod
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = _build_mod.LIB
+# ITM_CHECK_BOUNDS=1 selects the bounds-checked debug build (built by
+# build.build(checked=True)); the default is the release library
+LIB_PATH = _build_mod.LIB_CHECKED if os.environ.get("ITM_CHECK_BOUNDS") == "1" else _build_mod.LIB
 
 ITM_OK = 0
 ERRORS = {1: "ITM_ERR_ARG", 2: "ITM_ERR_CUDA", 3: "ITM_ERR_HASH_FULL", 4: "ITM_ERR_VBA_FULL",
           5: "ITM_ERR_RANGE", 6: "ITM_ERR_TIMEOUT", 7: "ITM_ERR_OVERFLOW", 8: "ITM_ERR_TOO_LARGE",
-          9: "ITM_ERR_SINGULAR"}
+          9: "ITM_ERR_SINGULAR", 10: "ITM_ERR_BOUNDS"}
 ITM_ERR_TOO_LARGE = 8
 ITM_NOALLOC_MAX_BLOCKS = 1 << 21
 ITM_MLP_FEATURES, ITM_MLP_HIDDEN, ITM_MLP_PARAMS = 52, 64, 7617

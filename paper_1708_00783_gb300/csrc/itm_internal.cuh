@@ -131,6 +131,21 @@ __device__ __forceinline__ unsigned long long entry_key(const int4 &e)
 
 // Sec. 3.3 retrieval through the read-only path (tables not modified by the
 // running kernel).  Returns the block index or -1.
+__device__ __forceinline__ void set_status(const SceneDev &s, uint32_t bits)
+{
+    atomicOr(&s.ctr->status, bits);
+}
+
+// Builds with -DITM_CHECK_BOUNDS check the indices into the hash table, the
+// voxel block array, the depth image and the per-frame lists before the
+// access; a failed check sets ITM_ST_BOUNDS and the access is skipped.  In
+// normal builds the checks compile to nothing.
+#ifdef ITM_CHECK_BOUNDS
+#define ITM_IN_BOUNDS(s, cond) ((cond) ? true : (set_status((s), ITM_ST_BOUNDS), false))
+#else
+#define ITM_IN_BOUNDS(s, cond) true
+#endif
+
 __device__ __forceinline__ int lookup_ro(const SceneDev &s, int bx, int by, int bz)
 {
     const unsigned long long key = pack_key(bx, by, bz);
@@ -138,8 +153,9 @@ __device__ __forceinline__ int lookup_ro(const SceneDev &s, int bx, int by, int 
     const int4 *E = reinterpret_cast<const int4 *>(s.entries);
     for (int guard = 0; guard <= s.ne; ++guard) {
         int4 e = __ldg(&E[idx]);
-        if (entry_key(e) == key && e.w >= 0) return e.w;
+        if (entry_key(e) == key && e.w >= 0) return ITM_IN_BOUNDS(s, e.w < s.nv) ? e.w : -1;
         if (e.z < 1) return -1;
+        if (!ITM_IN_BOUNDS(s, e.z - 1 < s.ne)) return -1;
         idx = s.nb + e.z - 1;
     }
     return -1;
@@ -153,8 +169,9 @@ __device__ __forceinline__ int lookup_cg(const SceneDev &s, int bx, int by, int 
     const int4 *E = reinterpret_cast<const int4 *>(s.entries);
     for (int guard = 0; guard <= s.ne; ++guard) {
         int4 e = __ldcg(&E[idx]);
-        if (entry_key(e) == key && e.w >= 0) return e.w;
+        if (entry_key(e) == key && e.w >= 0) return ITM_IN_BOUNDS(s, e.w < s.nv) ? e.w : -1;
         if (e.z < 1) return -1;
+        if (!ITM_IN_BOUNDS(s, e.z - 1 < s.ne)) return -1;
         idx = s.nb + e.z - 1;
     }
     return -1;
@@ -176,10 +193,6 @@ __device__ __forceinline__ float row_apply(const float *m, float x, float y, flo
 
 // --------------------------------------------------------------- atomics
 
-__device__ __forceinline__ void set_status(const SceneDev &s, uint32_t bits)
-{
-    atomicOr(&s.ctr->status, bits);
-}
 
 // Warp-aggregated append: the lanes active at the call each get a distinct
 // slot of their counter; lanes naming the same counter share one atomic

@@ -492,6 +492,7 @@ int itm_scene_status(itm_scene *sc)
     if (st.status & ITM_ST_RANGE) return ITM_ERR_RANGE;
     if (st.status & ITM_ST_TIMEOUT) return ITM_ERR_TIMEOUT;
     if (st.status & ITM_ST_OVERFLOW) return ITM_ERR_OVERFLOW;
+    if (st.status & ITM_ST_BOUNDS) return ITM_ERR_BOUNDS;
     return ITM_OK;
 }
 
