@@ -279,6 +279,22 @@ int itm_track_depth(const float *depth_dev, const itm_intrinsics *intr, int leve
  * are written).  Synchronises the stream. */
 int itm_mesh(itm_scene *scene, float *triangles_dev, int64_t capacity, int64_t *n_out, itm_stream stream);
 
+/* itm_allocate on an unsigned short millimetre frame: the allocation reads
+ * raw_dev (device uint16[height*width]) and converts each pixel as
+ * itm_depth_u16_to_f32 does (raw / 1000, correctly rounded, Sec. 4 view
+ * preparation), writing the float frame to depth_dev (device
+ * float[height*width], caller-owned) for the integration that follows: one
+ * pass over the frame instead of a separate conversion.  Same results as
+ * itm_depth_u16_to_f32 followed by itm_allocate. */
+int itm_allocate_u16(itm_scene *scene, const uint16_t *raw_dev, float *depth_dev, const itm_intrinsics *intr,
+                     const float T_wc[16], itm_stream stream);
+
+/* One frame from an unsigned short millimetre frame: itm_allocate_u16 (which
+ * writes depth_dev), itm_integrate on depth_dev and (when vertex_dev is not
+ * NULL) itm_raycast, on one stream. */
+int itm_process_frame_u16(itm_scene *scene, const uint16_t *raw_dev, float *depth_dev, const itm_intrinsics *intr,
+                          const float T_wc[16], float *vertex_dev, float *normal_dev, itm_stream stream);
+
 /* One frame of the per-frame core: itm_allocate, itm_integrate and (when
  * vertex_dev is not NULL) itm_raycast, on one stream. */
 int itm_process_frame(itm_scene *scene, const float *depth_dev, const itm_intrinsics *intr,

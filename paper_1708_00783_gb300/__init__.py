@@ -98,6 +98,8 @@ def _load():
         "itm_integrate_weighted": (I, [P, P, P, ip, fp16, P]),
         "itm_raycast": (I, [P, ip, fp16, P, P, P]),
         "itm_process_frame": (I, [P, P, ip, fp16, P, P, P]),
+        "itm_allocate_u16": (I, [P, P, P, ip, fp16, P]),
+        "itm_process_frame_u16": (I, [P, P, P, ip, fp16, P, P, P]),
         "itm_depth_u16_to_f32": (I, [P, P, ctypes.c_int64, P]),
         "itm_scene_stats": (I, [P, ctypes.POINTER(itm_stats)]),
         "itm_scene_status": (I, [P]),
@@ -296,6 +298,18 @@ def itm_track_depth(depth, intr, iters, dist_thresh, vertex, normal, ref_intr, T
                                 T.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(steps), _ptr(scratch),
                                 _stream(stream)), "itm_track_depth")
     return T.reshape(4, 4), steps.value
+
+
+def itm_allocate_u16(scene, raw, depth, intr, T_wc, stream=None):
+    a, p = _pose(T_wc)
+    _check(_lib.itm_allocate_u16(scene, _ptr(raw), _ptr(depth), ctypes.byref(intr), p, _stream(stream)),
+           "itm_allocate_u16")
+
+
+def itm_process_frame_u16(scene, raw, depth, intr, T_wc, vertex=None, normal=None, stream=None):
+    a, p = _pose(T_wc)
+    _check(_lib.itm_process_frame_u16(scene, _ptr(raw), _ptr(depth), ctypes.byref(intr), p, _ptr(vertex),
+                                      _ptr(normal), _stream(stream)), "itm_process_frame_u16")
 
 
 def itm_process_frame(scene, depth, intr, T_wc, vertex=None, normal=None, stream=None):

@@ -36,14 +36,16 @@ namespace {
 // Also clears the search-range tiles of this frame (n_range_tiles of them;
 // nothing reads them before the visible-list pass).
 __global__ void __launch_bounds__(256) alloc_enumerate_kernel(SceneDev s, const float *__restrict__ depth,
-                                                              Intr in, Mat34 T, float inv_b, int n_range_tiles)
+                                                              Intr in, Mat34 T, float inv_b, int n_range_tiles,
+                                                              const uint16_t *__restrict__ raw,
+                                                              float *__restrict__ depth_out)
 {
     const int cta = blockIdx.y * gridDim.x + blockIdx.x, ctas = gridDim.x * gridDim.y;
     for (int i = cta * blockDim.x + threadIdx.x; i < n_range_tiles; i += ctas * blockDim.x) {
         s.range_min[i] = 0xffffffffu;
         s.range_max[i] = 0u;
     }
-    enumerate_tile(s, depth, in, T, inv_b, blockIdx.x, blockIdx.y);
+    enumerate_tile(s, depth, in, T, inv_b, blockIdx.x, blockIdx.y, raw, depth_out);
 }
 
 // The last CTA to finish its requests then resolves the overflow list (its
@@ -115,7 +117,7 @@ int persistent_grid(int threads, const void *kernel)
 }  // namespace
 
 cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &in, const Mat34 &T_wc,
-                            const Mat34 &M_d, bool with_range, cudaStream_t st)
+                            const Mat34 &M_d, bool with_range, cudaStream_t st, const uint16_t *raw)
 {
     cudaError_t e = cudaMemsetAsync(reinterpret_cast<char *>(s.ctr) + kFrameCountersOffset, 0,
                                     kFrameCountersBytes, st);
@@ -123,7 +125,9 @@ cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &i
     const float inv_b = (float)(1.0 / (8.0 * (double)s.voxel_size));
     dim3 grid((in.W + 31) / 32, (in.H + 7) / 8);
     const int n_range_tiles = with_range ? ((in.W + 7) / 8) * ((in.H + 3) / 4) : 0;
-    alloc_enumerate_kernel<<<grid, 256, 0, st>>>(s, depth, in, T_wc, inv_b, n_range_tiles);
+    // with raw, depth is the output of the frame's conversion
+    alloc_enumerate_kernel<<<grid, 256, 0, st>>>(s, raw ? nullptr : depth, in, T_wc, inv_b, n_range_tiles, raw,
+                                                 raw ? const_cast<float *>(depth) : nullptr);
     static int g_commit = 0, g_visible = 0, g_visrange = 0;
     // one CTA per SM: a frame's requests (usually a few thousand) fit in one
     // pass, and fewer CTAs pay the completion count's fences

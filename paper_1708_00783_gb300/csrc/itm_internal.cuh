@@ -241,7 +241,7 @@ Intr to_intr(const itm_intrinsics *in);
 // Launchers implemented in the kernel translation units.
 namespace itm {
 cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &in, const Mat34 &T_wc,
-                            const Mat34 &M_d, bool with_range, cudaStream_t st);
+                            const Mat34 &M_d, bool with_range, cudaStream_t st, const uint16_t *raw = nullptr);
 cudaError_t launch_integrate(const SceneDev &s, const float *depth, const float *wpx, const Intr &in,
                              const Mat34 &M_d, cudaStream_t st);
 cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, const Mat34 &M_d, float4 *vtx,

@@ -190,10 +190,9 @@ int itm_scene_reset(itm_scene *sc, itm_stream stream)
     return check_cuda(launch_reset(sc->d, st));
 }
 
-int itm_allocate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
-                 itm_stream stream)
+static int allocate_impl(itm_scene *sc, const float *depth_dev, const uint16_t *raw_dev, const itm_intrinsics *intr,
+                         const float T_wc[16], itm_stream stream)
 {
-    Range range_("itm_allocate");
     if (!sc || !depth_dev || !valid_pose(T_wc) || !valid_intr(intr)) return ITM_ERR_ARG;
     Mat34 T, M;
     pose_rows(T_wc, T);
@@ -203,7 +202,7 @@ int itm_allocate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *in
     const Intr in = to_intr(intr);
     const bool with_range = range_fits(in);
     sc->alloc_epoch++;
-    const int r = check_cuda(launch_allocate(sc->d, depth_dev, in, T, M, with_range, st));
+    const int r = check_cuda(launch_allocate(sc->d, depth_dev, in, T, M, with_range, st, raw_dev));
     if (r == ITM_OK && with_range) {
         // the range tiles now hold the range of a raycast from this pose
         sc->range_epoch = sc->alloc_epoch;
@@ -211,6 +210,21 @@ int itm_allocate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *in
         sc->range_intr = *intr;
     }
     return r;
+}
+
+int itm_allocate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
+                 itm_stream stream)
+{
+    Range range_("itm_allocate");
+    return allocate_impl(sc, depth_dev, nullptr, intr, T_wc, stream);
+}
+
+int itm_allocate_u16(itm_scene *sc, const uint16_t *raw_dev, float *depth_dev, const itm_intrinsics *intr,
+                     const float T_wc[16], itm_stream stream)
+{
+    Range range_("itm_allocate_u16");
+    if (!raw_dev || !depth_dev) return ITM_ERR_ARG;
+    return allocate_impl(sc, depth_dev, raw_dev, intr, T_wc, stream);
 }
 
 int itm_integrate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
@@ -443,6 +457,17 @@ int itm_mesh(itm_scene *sc, float *triangles_dev, int64_t capacity, int64_t *n_o
     if (e != cudaSuccess) return check_cuda(e);
     *n_out = (int64_t)cnt;
     return (int64_t)cnt > capacity ? ITM_ERR_TOO_LARGE : ITM_OK;
+}
+
+int itm_process_frame_u16(itm_scene *sc, const uint16_t *raw_dev, float *depth_dev, const itm_intrinsics *intr,
+                          const float T_wc[16], float *vertex_dev, float *normal_dev, itm_stream stream)
+{
+    Range range_("itm_process_frame_u16");
+    if (!sc || (vertex_dev && !normal_dev)) return ITM_ERR_ARG;
+    int r = itm_allocate_u16(sc, raw_dev, depth_dev, intr, T_wc, stream);
+    if (r == ITM_OK) r = itm_integrate(sc, depth_dev, intr, T_wc, stream);
+    if (r == ITM_OK && vertex_dev) r = itm_raycast(sc, intr, T_wc, vertex_dev, normal_dev, stream);
+    return r;
 }
 
 int itm_process_frame(itm_scene *sc, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],

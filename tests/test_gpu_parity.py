@@ -246,6 +246,35 @@ def test_uint16_frames_give_the_same_volume(itm):
     compare_volumes(a.export(), b.export())
 
 
+@pytest.mark.parametrize("which", ["tiny", "kinect"])
+def test_fused_u16_allocation_equals_conversion_then_allocation(itm, which):
+    """itm_process_frame_u16 (the frame converted inside the allocation) gives
+    the float frame of itm_depth_u16_to_f32, the same volume and the same
+    raycast maps, bit for bit, frame after frame (with holes and ragged
+    edges in the Kinect frames)."""
+    import torch
+    w = tiny_workload(n_frames=4) if which == "tiny" else kinect_workload(seed=6)
+    ci = intr_of(itm, w.intr)
+    H, W = w.intr.height, w.intr.width
+    a = itm.Scene(**w.params)
+    b = itm.Scene(**w.params)
+    maps = [torch.zeros((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(4)]
+    for k in range(4):
+        f = w.frame(k)
+        raw = dev(f.depth_u16.view(np.int16))
+        da = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        db = torch.full((H, W), np.nan, dtype=torch.float32, device="cuda")
+        itm.itm_depth_u16_to_f32(raw, da)
+        a.process(da, ci, f.T_wc, maps[0], maps[1])
+        itm.itm_process_frame_u16(b.handle, raw, db, ci, f.T_wc, maps[2], maps[3])
+        torch.cuda.synchronize()
+        assert torch.equal(da, db)
+        assert torch.equal(maps[0], maps[2]) and torch.equal(maps[1], maps[3])
+    assert a.status() == 0 and b.status() == 0
+    rep = compare_volumes(a.export(), b.export())
+    assert rep["sdf_bitexact_frac"] == 1.0
+
+
 @pytest.mark.slow
 def test_kinect_scale_frames(itm):
     """Full 640x480, 5 mm voxels, 2^20 buckets: the configuration the
