@@ -362,8 +362,12 @@ uint32_t itm_hash_index(int x, int y, int z, int num_buckets);
 int itm_mlp_pack(const float *params_dev, void *packed_dev, itm_stream stream);
 
 /* w_px for every pixel of a depth frame (device float[height*width]) with
- * the packed network: features in fp32, both hidden layers on the tensor
- * cores with bf16 operands and fp32 accumulation, output layer in fp32. */
+ * the packed network: features in fp32, both hidden layers as tcgen05
+ * tensor-core products (bf16 operands, fp32 accumulators in tensor memory),
+ * output layer in fp32.  Argument errors return ITM_ERR_ARG (packed_dev must
+ * be 16-byte aligned).  Completion of each product is awaited with a bounded
+ * wait; a wait that gives up (not expected on a healthy device) leaves NaN
+ * weights in the tiles concerned, which itm_integrate_weighted skips. */
 int itm_conf_weights(const float *depth_dev, const itm_intrinsics *intr, float mu, const void *packed_dev,
                      float *wpx_dev, itm_stream stream);
 

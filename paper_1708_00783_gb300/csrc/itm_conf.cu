@@ -15,21 +15,26 @@
 //   parameters (fp32 master copy, 7617): W1[64][52], b1, W2[64][64], b2, w3, b3.
 //
 // Inference (conf_weights_kernel): 128-thread CTAs over 16x8-pixel tiles.
-// The depth tile and its 3-pixel halo are staged in shared memory, each
-// thread writes its pixel's 52 features as bfloat16 into a 128x64 A tile
-// (zero padded), and each warp multiplies its 32 pixels through both layers
-// on the tensor cores (mma.sync m16n8k16, bf16 operands, fp32 accumulation).
-// The fp32 accumulators of layer 1 are exactly the A fragments of layer 2
-// after bias, ReLU and rounding to bfloat16, so h1 never leaves registers.
-// The 64-wide dot product of layer 3 runs in fp32 with two shuffles.  The
-// packed weights (bf16 W1 padded to 64x64, bf16 W2, fp32 biases and w3) sit
-// in shared memory for the CTA's whole persistent loop.
+// The depth tile and its 3-pixel halo are staged in shared memory and each
+// thread writes its pixel's 52 features, rounded to bfloat16 and zero padded
+// to 64, as one row of the tile's 128 x 64 A operand.  Both hidden layers are
+// 5th-generation tensor-core products (tcgen05.mma, M=128, N=64, K=64, bf16
+// operands from shared memory, fp32 accumulators in 64 TMEM columns) issued
+// by one thread and completed through an mbarrier.  Each thread reads its
+// pixel's accumulator row back from TMEM (its warp's lane quarter), adds the
+// bias and applies the ReLU; after layer 1 the rounded row overwrites the
+// pixel's A row as layer 2's input, after layer 2 the 64-term output dot
+// product and the sigmoid run in fp32 in the same thread.  The packed weights
+// sit in shared memory, in the tensor core's canonical layout, for the CTA's
+// whole persistent loop.
 //
 // Training: features of sampled pixels (conf_features_kernel), a per-sample
 // forward/backward in fp32 with the same bfloat16-rounded weights and inputs
 // as inference (the rounding is taken as the identity for the gradient),
 // a gradient reduction over the batch, and Adam on the fp32 master copy.
 #include <cuda_bf16.h>
+
+#include <algorithm>
 
 #include "itm_internal.cuh"
 
@@ -66,6 +71,40 @@ struct TileDepth {
     __device__ float operator()(int u, int v) const { return S[(v - v0 + 3) * stride + (u - u0 + 3)]; }
 };
 
+// patch entry k < 49: row offset i = k / 7 - 3, column offset j = k % 7 - 3
+template <class Depth>
+__device__ __forceinline__ float patch_feature(const Depth &D, int u, int v, float dc, float inv_mu, int k)
+{
+    const float d = D(u + k % 7 - 3, v + k / 7 - 3);
+    return d > 0.0f ? fminf(fmaxf((d - dc) * inv_mu, -4.0f), 4.0f) : 0.0f;
+}
+
+// entries 49..51: the unit normal from central differences, or 0; rfx and
+// rfy are 1 / fx and 1 / fy
+template <class Depth>
+__device__ __forceinline__ void normal_feature(const Depth &D, const Intr &in, float rfx, float rfy, int u, int v,
+                                               float (&n)[3])
+{
+    n[0] = n[1] = n[2] = 0.0f;
+    const float dl = D(u - 1, v), dr = D(u + 1, v), du = D(u, v - 1), dd = D(u, v + 1);
+    if (dl > 0.0f && dr > 0.0f && du > 0.0f && dd > 0.0f) {
+        const float xl = ((float)(u - 1) - in.cx) * rfx, xc = ((float)u - in.cx) * rfx;
+        const float xr = ((float)(u + 1) - in.cx) * rfx;
+        const float yu = ((float)(v - 1) - in.cy) * rfy, yc = ((float)v - in.cy) * rfy;
+        const float yd = ((float)(v + 1) - in.cy) * rfy;
+        const float ax = dd * xc - du * xc, ay = dd * yd - du * yu, az = dd - du;  // along +v
+        const float bx = dr * xr - dl * xl, by = dr * yc - dl * yc, bz = dr - dl;  // along +u
+        const float nx = ay * bz - az * by, ny = az * bx - ax * bz, nz = ax * by - ay * bx;
+        const float l = sqrtf(nx * nx + ny * ny + nz * nz);
+        if (l > 0.0f) {
+            const float r = 1.0f / l;
+            n[0] = nx * r;
+            n[1] = ny * r;
+            n[2] = nz * r;
+        }
+    }
+}
+
 template <class Depth>
 __device__ __forceinline__ bool conf_features(const Depth &D, const Intr &in, float mu, int u, int v, float *x)
 {
@@ -75,37 +114,20 @@ __device__ __forceinline__ bool conf_features(const Depth &D, const Intr &in, fl
     if (!(dc > 0.0f)) return false;
     const float inv_mu = 1.0f / mu;
 #pragma unroll
-    for (int i = -3; i <= 3; ++i)
-#pragma unroll
-        for (int j = -3; j <= 3; ++j) {
-            const float d = D(u + j, v + i);
-            float f = 0.0f;
-            if (d > 0.0f) f = fminf(fmaxf((d - dc) * inv_mu, -4.0f), 4.0f);
-            x[(i + 3) * 7 + (j + 3)] = f;
-        }
-    const float dl = D(u - 1, v), dr = D(u + 1, v), du = D(u, v - 1), dd = D(u, v + 1);
-    if (dl > 0.0f && dr > 0.0f && du > 0.0f && dd > 0.0f) {
-        const float Plx = dl * ((float)(u - 1) - in.cx) / in.fx, Ply = dl * ((float)v - in.cy) / in.fy;
-        const float Prx = dr * ((float)(u + 1) - in.cx) / in.fx, Pry = dr * ((float)v - in.cy) / in.fy;
-        const float Pux = du * ((float)u - in.cx) / in.fx, Puy = du * ((float)(v - 1) - in.cy) / in.fy;
-        const float Pdx = dd * ((float)u - in.cx) / in.fx, Pdy = dd * ((float)(v + 1) - in.cy) / in.fy;
-        const float ax = Pdx - Pux, ay = Pdy - Puy, az = dd - du;  // along +v
-        const float bx = Prx - Plx, by = Pry - Ply, bz = dr - dl;  // along +u
-        const float nx = ay * bz - az * by, ny = az * bx - ax * bz, nz = ax * by - ay * bx;
-        const float l = sqrtf(nx * nx + ny * ny + nz * nz);
-        if (l > 0.0f) {
-            x[49] = nx / l;
-            x[50] = ny / l;
-            x[51] = nz / l;
-        }
-    }
+    for (int k = 0; k < 49; ++k) x[k] = patch_feature(D, u, v, dc, inv_mu, k);
+    float n[3];
+    normal_feature(D, in, 1.0f / in.fx, 1.0f / in.fy, u, v, n);
+    x[49] = n[0];
+    x[50] = n[1];
+    x[51] = n[2];
     return true;
 }
 
 // --------------------------------------------------------------- inference
 
 constexpr int kTW = 16, kTH = 8, kHW = kTW + 6, kHH = kTH + 6;
-constexpr int kStride = 72;  // bf16 per shared-memory row (64 + 8 pad: conflict-free fragment loads)
+constexpr int kRows = kTW * kTH;  // pixels per tile = rows of the A operand = TMEM lanes
+static_assert(kRows == 128 && NH == 64, "one M=128, N=64, K=64 product per layer and tile");
 
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
 {
@@ -113,135 +135,279 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi)
     return *reinterpret_cast<const uint32_t *>(&p);
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
-                                         uint32_t b1)
+// ---- tcgen05 glue (inline PTX).  Operands sit in shared memory in the
+// canonical K-major layout without swizzle: 8-row x 16-byte core matrices,
+// the two core matrices of one K=16 step 128 B apart (leading byte offset),
+// consecutive 8-row groups 1024 B apart (stride byte offset).
+
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// byte offset of row r, elements 8 kc .. 8 kc + 7, in a 64-wide bf16 operand
+__device__ __forceinline__ uint32_t canon_off(int r, int kc) { return (r >> 3) * 1024 + kc * 128 + (r & 7) * 16; }
+
+// shared-memory matrix descriptor: start >> 4, leading and stride byte
+// offsets >> 4, bit 46 the descriptor version; base offset 0, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
 {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           (1ull << 46);
 }
 
-constexpr size_t kConfSmem = (size_t)(2 * NH + kTW * kTH) * kStride * 2 + (3 * NH + 4) * 4 + kHH * kHW * 4 + 128;
+// instruction descriptor of kind::f16: fp32 D (bit 4), bf16 A (bits 7-9) and
+// B (bits 10-12), both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NH >> 3) << 17) |
+                            ((uint32_t)(kRows >> 4) << 24);
+
+// D[128 x 64] (TMEM, fp32) = A[128 x 64] B[64 x 64]^T as four K=16 steps;
+// completion (operands read, D written) arrives on the mbarrier
+__device__ __forceinline__ void mma_layer(uint32_t tmem, uint32_t a, uint32_t b, uint32_t bar)
+{
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const uint64_t ad = smem_desc(a + 256 * k), bd = smem_desc(b + 256 * k);
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(kIdesc), "r"(k > 0 ? 1u : 0u));
+    }
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+constexpr int kWaitSpins = 1 << 20;
+
+constexpr int kStage = (kHH * kHW + 127) / 128;  // depth values a thread stages per tile
+
+// depth of tile's pixels and their 3-pixel halo, entry i = tid + 128 j of the
+// row-major (kTH + 6) x (kTW + 6) patch; 0 outside the image and where D <= 0
+__device__ __forceinline__ void fetch_depth(const float *__restrict__ depth, const Intr &in, int tiles_x, int tile,
+                                            int tid, float (&pre)[kStage])
+{
+    const int u0 = (tile % tiles_x) * kTW - 3, v0 = (tile / tiles_x) * kTH - 3;
+#pragma unroll
+    for (int j = 0; j < kStage; ++j) {
+        const int i = tid + 128 * j, u = u0 + i % kHW, v = v0 + i / kHW;
+        float d = 0.0f;
+        if (i < kHH * kHW && u >= 0 && v >= 0 && u < in.W && v < in.H) d = __ldg(&depth[(size_t)v * in.W + u]);
+        pre[j] = d > 0.0f ? d : 0.0f;
+    }
+}  // try_wait rounds before a wait is given up
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity)
+{
+    for (int it = 0; it < kWaitSpins; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n"
+            " selp.b32 %0, 1, 0, P1;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__device__ __forceinline__ void tc_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void async_proxy_fence() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// the warp's 32 lanes x 32 fp32 columns of D from column taddr: thread t of
+// warp w gets row 32 w + t
+__device__ __forceinline__ void tmem_row32(uint32_t taddr, float (&d)[32])
+{
+    uint32_t r[32];
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[16 * c]), "=r"(r[16 * c + 1]), "=r"(r[16 * c + 2]), "=r"(r[16 * c + 3]), "=r"(r[16 * c + 4]),
+              "=r"(r[16 * c + 5]), "=r"(r[16 * c + 6]), "=r"(r[16 * c + 7]), "=r"(r[16 * c + 8]),
+              "=r"(r[16 * c + 9]), "=r"(r[16 * c + 10]), "=r"(r[16 * c + 11]), "=r"(r[16 * c + 12]),
+              "=r"(r[16 * c + 13]), "=r"(r[16 * c + 14]), "=r"(r[16 * c + 15])
+            : "r"(taddr + 16 * c));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    // the registers are defined again after the wait, so no use moves above it
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+        asm volatile(""
+                     : "+r"(r[16 * c]), "+r"(r[16 * c + 1]), "+r"(r[16 * c + 2]), "+r"(r[16 * c + 3]),
+                       "+r"(r[16 * c + 4]), "+r"(r[16 * c + 5]), "+r"(r[16 * c + 6]), "+r"(r[16 * c + 7]),
+                       "+r"(r[16 * c + 8]), "+r"(r[16 * c + 9]), "+r"(r[16 * c + 10]), "+r"(r[16 * c + 11]),
+                       "+r"(r[16 * c + 12]), "+r"(r[16 * c + 13]), "+r"(r[16 * c + 14]), "+r"(r[16 * c + 15]));
+#pragma unroll
+    for (int i = 0; i < 32; ++i) d[i] = __uint_as_float(r[i]);
+}
+
+// dynamic shared memory: W1, W2 and the A tile in the canonical layout, then
+// b1, b2, w3, b3 (fp32), the depth tile with its halo and the valid flags
+constexpr size_t kOffSW1 = 0, kOffSW2 = NH * 64 * 2, kOffSA = 2 * NH * 64 * 2;
+constexpr size_t kOffSF = kOffSA + kRows * 64 * 2;
+constexpr size_t kOffSD = kOffSF + (3 * NH + 4) * 4;
+constexpr size_t kOffSV = kOffSD + kHH * kHW * 4;
+constexpr size_t kConfSmem = kOffSV + kRows;
+constexpr int kTmemCols = 64;  // both layers' accumulators, one after the other
+// at most 8 CTAs per SM (228 KB of shared memory, 1 KB reserved per CTA), so
+// their TMEM columns fit the SM's 512 and no allocation waits
+static_assert(9 * (kConfSmem + 1024) > 228 * 1024 && 8 * kTmemCols <= 512, "TMEM budget");
 
 __global__ void __launch_bounds__(128) conf_weights_kernel(const float *__restrict__ depth, Intr in, float mu,
                                                            const unsigned char *__restrict__ packed,
                                                            float *__restrict__ wpx, int tiles_x, int n_tiles)
 {
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16 *sW1 = reinterpret_cast<__nv_bfloat16 *>(smem);
-    __nv_bfloat16 *sW2 = sW1 + NH * kStride;
-    __nv_bfloat16 *sA = sW2 + NH * kStride;
-    float *sB1 = reinterpret_cast<float *>(sA + kTW * kTH * kStride);
-    float *sB2 = sB1 + NH, *sW3 = sB2 + NH, *sB3 = sW3 + NH;
-    float *sD = sB3 + 4;
-    unsigned char *sValid = reinterpret_cast<unsigned char *>(sD + kHH * kHW);
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_slot;
+    const float *sB1 = reinterpret_cast<const float *>(smem + kOffSF);
+    const float *sB2 = sB1 + NH, *sW3 = sB2 + NH, *sB3 = sW3 + NH;
+    float *sD = reinterpret_cast<float *>(smem + kOffSD);
+    unsigned char *sValid = smem + kOffSV;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const uint32_t sbase = smem_addr(smem), bar_a = smem_addr(&bar);
+    // the next tile's depth is loaded into registers while this one computes
+    // (the first tile's while the weights are staged)
+    float pre[kStage];
+    if (blockIdx.x < n_tiles) fetch_depth(depth, in, tiles_x, blockIdx.x, tid, pre);
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = lane >> 2, t4 = lane & 3;
     {
-        const __nv_bfloat16 *W1p = reinterpret_cast<const __nv_bfloat16 *>(packed + kOffW1);
-        const __nv_bfloat16 *W2p = reinterpret_cast<const __nv_bfloat16 *>(packed + kOffW2);
-        for (int i = tid; i < NH * 64; i += 128) {
-            sW1[(i >> 6) * kStride + (i & 63)] = W1p[i];
-            sW2[(i >> 6) * kStride + (i & 63)] = W2p[i];
+        // weights: 16-byte chunks of the row-major 64 x 64 matrices
+        const uint4 *W = reinterpret_cast<const uint4 *>(packed + kOffW1);
+        for (int j = tid; j < 2 * NH * 8; j += 128) {
+            const int m = j >> 9, n = (j >> 3) & 63, kc = j & 7;
+            *reinterpret_cast<uint4 *>(smem + (m ? kOffSW2 : kOffSW1) + canon_off(n, kc)) = __ldg(&W[j]);
         }
         const float *f32 = reinterpret_cast<const float *>(packed + kOffB1);
-        for (int i = tid; i < 3 * NH + 1; i += 128) sB1[i] = f32[i];  // b1, b2, w3, b3 are contiguous
+        float *dst = reinterpret_cast<float *>(smem + kOffSF);
+        for (int i = tid; i < 3 * NH + 1; i += 128) dst[i] = f32[i];  // b1, b2, w3, b3 are contiguous
     }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
+    async_proxy_fence();
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "n"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_before_sync();
     __syncthreads();
+    tc_after_sync();
+    const uint32_t tmem = tmem_slot;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's TMEM lane quarter
 
+    // A wait that gives up is voted warp-uniform (the TMEM reads are warp
+    // collectives) and reaches the whole CTA at its next barrier.
+    int failed_tile = -1, last_tile = -1;
+    uint32_t failed_parity = 0;
+    bool pending = false;  // this warp's layer-2 wait gave up
+    const float rfx = 1.0f / in.fx, rfy = 1.0f / in.fy, inv_mu = 1.0f / mu;
     for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
         const int u0 = (tile % tiles_x) * kTW, v0 = (tile / tiles_x) * kTH;
-        for (int i = tid; i < kHH * kHW; i += 128) {
-            const int u = u0 + (i % kHW) - 3, v = v0 + (i / kHW) - 3;
-            float d = 0.0f;
-            if (u >= 0 && v >= 0 && u < in.W && v < in.H) {
-                d = __ldg(&depth[(size_t)v * in.W + u]);
-                if (!(d > 0.0f)) d = 0.0f;
-            }
-            sD[i] = d;
+#pragma unroll
+        for (int j = 0; j < kStage; ++j)
+            if (tid + 128 * j < kHH * kHW) sD[tid + 128 * j] = pre[j];
+        if (tile + (int)gridDim.x < n_tiles) fetch_depth(depth, in, tiles_x, tile + gridDim.x, tid, pre);
+        if (__syncthreads_or(pending)) {
+            failed_tile = last_tile;
+            failed_parity = 1;
+            break;
         }
-        __syncthreads();
+        const int u = u0 + (tid & (kTW - 1)), v = v0 + tid / kTW;
         {
-            const int u = u0 + (tid & (kTW - 1)), v = v0 + tid / kTW;
-            float x[NF];
+            // the pixel's features, rounded to bf16, 8 at a time into its A row
             const TileDepth D{sD, u0, v0, kHW};
-            const bool ok = (u < in.W && v < in.H) && conf_features(D, in, mu, u, v, x);
+            const float dc = D(u, v);
+            const bool ok = u < in.W && v < in.H && dc > 0.0f;
             sValid[tid] = ok;
-            uint32_t *row = reinterpret_cast<uint32_t *>(sA + tid * kStride);
+            float n[3] = {0.0f, 0.0f, 0.0f};
+            if (ok) normal_feature(D, in, rfx, rfy, u, v, n);
 #pragma unroll
-            for (int k = 0; k < 32; ++k) row[k] = (2 * k + 1 < NF) ? pack_bf16(x[2 * k], x[2 * k + 1]) : 0u;
-        }
-        __syncthreads();
-
-#pragma unroll 1
-        for (int mt = 0; mt < 2; ++mt) {
-            const int r0 = warp * 32 + mt * 16;
-            float acc[8][4];
+            for (int kc = 0; kc < 8; ++kc) {
+                float f[8];
 #pragma unroll
-            for (int n = 0; n < 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
-            const uint32_t *A = reinterpret_cast<const uint32_t *>(sA);
-            const uint32_t *B1 = reinterpret_cast<const uint32_t *>(sW1);
-            const uint32_t *B2 = reinterpret_cast<const uint32_t *>(sW2);
-            constexpr int RW = kStride / 2;  // 32-bit words per row
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const uint32_t a0 = A[(r0 + g) * RW + kk * 8 + t4], a1 = A[(r0 + g + 8) * RW + kk * 8 + t4];
-                const uint32_t a2 = A[(r0 + g) * RW + kk * 8 + 4 + t4], a3 = A[(r0 + g + 8) * RW + kk * 8 + 4 + t4];
-#pragma unroll
-                for (int n = 0; n < 8; ++n) {
-                    const uint32_t b0 = B1[(n * 8 + g) * RW + kk * 8 + t4], b1 = B1[(n * 8 + g) * RW + kk * 8 + 4 + t4];
-                    mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+                for (int q = 0; q < 8; ++q) {
+                    const int k = 8 * kc + q;
+                    f[q] = k < 49 ? patch_feature(D, u, v, dc, inv_mu, k) : (k < NF ? n[k - 49] : 0.0f);
+                    if (!ok) f[q] = 0.0f;
                 }
-            }
-            // bias + ReLU + bf16: the accumulators become layer-2 A fragments
-            uint32_t h[4][4];
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                const int c0 = (2 * kk) * 8 + 2 * t4, c1 = (2 * kk + 1) * 8 + 2 * t4;
-                h[kk][0] = pack_bf16(fmaxf(acc[2 * kk][0] + sB1[c0], 0.f), fmaxf(acc[2 * kk][1] + sB1[c0 + 1], 0.f));
-                h[kk][1] = pack_bf16(fmaxf(acc[2 * kk][2] + sB1[c0], 0.f), fmaxf(acc[2 * kk][3] + sB1[c0 + 1], 0.f));
-                h[kk][2] =
-                    pack_bf16(fmaxf(acc[2 * kk + 1][0] + sB1[c1], 0.f), fmaxf(acc[2 * kk + 1][1] + sB1[c1 + 1], 0.f));
-                h[kk][3] =
-                    pack_bf16(fmaxf(acc[2 * kk + 1][2] + sB1[c1], 0.f), fmaxf(acc[2 * kk + 1][3] + sB1[c1 + 1], 0.f));
-            }
-#pragma unroll
-            for (int n = 0; n < 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-#pragma unroll
-                for (int n = 0; n < 8; ++n) {
-                    const uint32_t b0 = B2[(n * 8 + g) * RW + kk * 8 + t4], b1 = B2[(n * 8 + g) * RW + kk * 8 + 4 + t4];
-                    mma_bf16(acc[n], h[kk][0], h[kk][1], h[kk][2], h[kk][3], b0, b1);
-                }
-            }
-            float olo = 0.0f, ohi = 0.0f;
-#pragma unroll
-            for (int n = 0; n < 8; ++n) {
-                const int c = n * 8 + 2 * t4;
-                olo += sW3[c] * fmaxf(acc[n][0] + sB2[c], 0.f) + sW3[c + 1] * fmaxf(acc[n][1] + sB2[c + 1], 0.f);
-                ohi += sW3[c] * fmaxf(acc[n][2] + sB2[c], 0.f) + sW3[c + 1] * fmaxf(acc[n][3] + sB2[c + 1], 0.f);
-            }
-            olo += __shfl_xor_sync(kFull, olo, 1);
-            olo += __shfl_xor_sync(kFull, olo, 2);
-            ohi += __shfl_xor_sync(kFull, ohi, 1);
-            ohi += __shfl_xor_sync(kFull, ohi, 2);
-            if (t4 == 0) {
-#pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    const int p = r0 + g + 8 * half;
-                    const int u = u0 + (p & (kTW - 1)), v = v0 + p / kTW;
-                    if (u < in.W && v < in.H) {
-                        const float o = (half ? ohi : olo) + sB3[0];
-                        wpx[(size_t)v * in.W + u] = sValid[p] ? 1.0f / (1.0f + expf(-o)) : 0.0f;
-                    }
-                }
+                *reinterpret_cast<uint4 *>(smem + kOffSA + canon_off(tid, kc)) =
+                    make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]), pack_bf16(f[6], f[7]));
             }
         }
+        // layer 1: the A tile and the weights to the tensor core
+        async_proxy_fence();
+        tc_before_sync();
         __syncthreads();
+        if (tid == 0) {
+            tc_after_sync();
+            mma_layer(tmem, sbase + kOffSA, sbase + kOffSW1, bar_a);
+        }
+        bool ok = __all_sync(kFull, mbar_wait(bar_a, 0));
+        tc_after_sync();
+        // h1 = bf16(relu(acc + b1)) is layer 2's A tile, in place of x
+#pragma unroll
+        for (int half = 0; half < 2 && ok; ++half) {
+            float h[32];
+            tmem_row32(lane_base + 32 * half, h);
+#pragma unroll
+            for (int kc = 0; kc < 4; ++kc) {
+                uint32_t w[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int i = 8 * kc + 2 * q, n = 32 * half + i;
+                    w[q] = pack_bf16(fmaxf(h[i] + sB1[n], 0.0f), fmaxf(h[i + 1] + sB1[n + 1], 0.0f));
+                }
+                *reinterpret_cast<uint4 *>(smem + kOffSA + canon_off(tid, 4 * half + kc)) =
+                    make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        }
+        async_proxy_fence();
+        tc_before_sync();
+        if (__syncthreads_or(!ok)) {
+            failed_tile = tile;
+            failed_parity = 0;
+            break;
+        }
+        if (tid == 0) {
+            tc_after_sync();
+            mma_layer(tmem, sbase + kOffSA, sbase + kOffSW2, bar_a);
+        }
+        ok = __all_sync(kFull, mbar_wait(bar_a, 1));
+        pending = !ok;
+        last_tile = tile;
+        tc_after_sync();
+        if (ok) {
+            float o = 0.0f;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float h[32];
+                tmem_row32(lane_base + 32 * half, h);
+#pragma unroll
+                for (int i = 0; i < 32; ++i) o += sW3[32 * half + i] * fmaxf(h[i] + sB2[32 * half + i], 0.0f);
+            }
+            o += sB3[0];
+            if (u < in.W && v < in.H) wpx[(size_t)v * in.W + u] = sValid[tid] ? 1.0f / (1.0f + expf(-o)) : 0.0f;
+        }
+        tc_before_sync();  // this tile's TMEM reads come before the next tile's products
+    }
+    if (failed_tile < 0 && __syncthreads_or(pending)) {
+        failed_tile = last_tile;
+        failed_parity = 1;
+    }
+    if (failed_tile >= 0) {
+        // a product that never signalled completion: NaN weights for the
+        // CTA's remaining pixels (weighted integration skips them), one more
+        // bounded wait for the product in flight, then the TMEM is freed
+        for (int tile = failed_tile; tile < n_tiles; tile += gridDim.x) {
+            const int u = (tile % tiles_x) * kTW + (tid & (kTW - 1)), v = (tile / tiles_x) * kTH + tid / kTW;
+            if (u < in.W && v < in.H) wpx[(size_t)v * in.W + u] = __int_as_float(0x7fc00000);
+        }
+        mbar_wait(bar_a, failed_parity);
+    }
+    tc_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc_after_sync();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols) : "memory");
     }
 }
 
@@ -381,16 +547,26 @@ __global__ void adam_kernel(float *__restrict__ P, const float *__restrict__ g, 
     P[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
+// CTAs of conf_weights_kernel resident per SM, counted from its registers,
+// shared memory and TMEM columns (the runtime's occupancy calculator answers
+// one CTA per SM for this kernel), times the SM count
 int conf_grid()
 {
     static int g = 0;
     if (!g) {
-        int dev = 0, sms = 1, per = 1;
+        int dev = 0, sms = 1, regs_sm = 65536, smem_sm = 0, reserved = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(conf_weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConfSmem);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, conf_weights_kernel, 128, kConfSmem);
-        g = sms * (per > 0 ? per : 1);
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, conf_weights_kernel);
+        const int regs_cta = (fa.numRegs + 7) / 8 * 8 * 128;  // registers are allocated 256 per warp
+        int per = 512 / kTmemCols;
+        if (regs_cta > 0) per = std::min(per, regs_sm / regs_cta);
+        per = std::min(per, (int)(smem_sm / (kConfSmem + fa.sharedSizeBytes + (size_t)reserved)));
+        g = sms * std::max(per, 1);
     }
     return g;
 }
