@@ -166,7 +166,7 @@ def committed_traffic():
         d = json.load(f)
     if d.get("integrate_source_sha256_16") != integrate_source_hash():
         return None
-    return d.get("dram_bytes_per_launch_scaled")
+    return d.get("dram_bytes_per_launch_mean")
 
 
 class ClockSampler:
