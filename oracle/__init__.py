@@ -8,7 +8,8 @@ single-threaded, fp32 with every operation rounded separately, as the paper's
 listings are written in float); this module only marshals numpy arrays.
 
 Every function here is pinned by tests in ``tests/test_oracle_pins.py``,
-``tests/test_oracle_conf_pins.py`` and ``tests/test_oracle_combined_pins.py``
+``tests/test_oracle_conf_pins.py``, ``tests/test_oracle_combined_pins.py``
+and ``tests/test_oracle_swap_pins.py``
 against closed forms, brute force and analytic geometry; see the docstrings
 there for which pin covers which step.
 """
@@ -106,6 +107,16 @@ def _load():
     lib.orc_cell_triangles.argtypes = [f32p, i32p_]
     lib.orc_track.restype = I
     lib.orc_track.argtypes = [f32p, I, I, f32p, I, i32p_, f32p, f32p, f32p, I, I, f32p, f32p, f32p]
+    lib.orc_swap_enable.restype = I
+    lib.orc_swap_enable.argtypes = [P, I, I]
+    lib.orc_swap_in.restype = I
+    lib.orc_swap_in.argtypes = [P]
+    lib.orc_swap_out.restype = I
+    lib.orc_swap_out.argtypes = [P]
+    i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+    lib.orc_swap_counters.argtypes = [P, i64p]
+    lib.orc_swap_export_host.restype = I
+    lib.orc_swap_export_host.argtypes = [P, P, P, P, P, I]
     _lib = lib
     return lib
 
@@ -207,6 +218,37 @@ class Scene:
         out = np.zeros((max(n, 1), 3, 3), dtype=np.float32)
         _load().orc_mesh(self.p, out.ctypes.data, n)
         return out[:n]
+
+    # Sec. 5 swapping (readings in itm_oracle.c above orc_swap_enable)
+    SW_HOST, SW_MERGE = 1, 2
+
+    def swap_enable(self, transfer_blocks, idle_frames=1):
+        if _load().orc_swap_enable(self.p, int(transfer_blocks), int(idle_frames)) != 0:
+            raise ValueError("swapping already on or invalid arguments")
+
+    def swap_in(self) -> int:
+        return int(_load().orc_swap_in(self.p))
+
+    def swap_out(self) -> int:
+        return int(_load().orc_swap_out(self.p))
+
+    def swap_counters(self) -> dict:
+        out = np.zeros(5, dtype=np.int64)
+        _load().orc_swap_counters(self.p, out)
+        return dict(host_data=int(out[0]), swapped_out=int(out[1]), waiting=int(out[2]),
+                    moved_in=int(out[3]), moved_out=int(out[4]))
+
+    def swap_export_host(self):
+        """(coords int16 [n,3], sdf float32 [n,512], w float32 [n,512], state
+        int32 [n]) of the blocks with host data, in entry order."""
+        lib = _load()
+        n = int(lib.orc_swap_export_host(self.p, None, None, None, None, 0))
+        coords = np.zeros((max(n, 1), 3), dtype=np.int16)
+        sdf = np.zeros((max(n, 1), 512), dtype=np.float32)
+        w = np.zeros((max(n, 1), 512), dtype=np.float32)
+        st = np.zeros(max(n, 1), dtype=np.int32)
+        lib.orc_swap_export_host(self.p, coords.ctypes.data, sdf.ctypes.data, w.ctypes.data, st.ctypes.data, n)
+        return coords[:n], sdf[:n], w[:n], st[:n]
 
     def set_block(self, b, sdf, w):
         """Allocate block b (if missing) and set its 512 voxels (x + 8y + 64z)."""

@@ -27,6 +27,11 @@
  *                         the raycast maps, Gauss-Newton steps, pyramid
  *   orc_mesh              Sec. 4 Marching Cubes over the allocated blocks
  *   orc_depth_u16_to_f32  Sec. 4 (ViewBuilder: unsigned short -> float depth)
+ *   orc_swap_*            Sec. 5 swapping: a host block store with one slot
+ *                         per hash entry, entries of swapped-out blocks kept
+ *                         with ptr -1, at most K blocks moved per call, and
+ *                         the secondary fusion of host data into a device
+ *                         block that went on integrating meanwhile
  *
  * Readings taken where the paper is silent (each one is also listed in the
  * repository's design notes):
@@ -42,7 +47,8 @@
  *     an optimisation that must not change the result);
  *   - depth that is not > 0 (zero, negative or NaN) is no measurement;
  *   - learned weights: newW = w_px instead of 1, skipped when w_px <= 0;
- *   - raycast: see the comment above orc_raycast.
+ *   - raycast: see the comment above orc_raycast;
+ *   - swapping: see the comment above orc_swap_enable.
  */
 #include <math.h>
 #include <stdint.h>
@@ -80,7 +86,20 @@ typedef struct {
     int32_t *alloc_order; /* block indices in order of allocation */
     int n_alloc;
     int status;
+    /* Sec. 5 swapping, off until orc_swap_enable */
+    int swap_on, swap_k, swap_idle;
+    int frame;            /* allocations since swapping was enabled */
+    uint8_t *swap_state;  /* per entry: ORC_SW_* */
+    int32_t *touch;       /* per entry: last allocation whose segments met the block */
+    float **host;         /* per entry: the host slot (512 sdf then 512 weights), made on first use */
+    long long swapped_in, swapped_out;
 } orc_scene;
+
+enum {
+    ORC_SW_DEVICE = 0, /* the block's current data is in the device block (or it has none) */
+    ORC_SW_HOST = 1,   /* swapped out: the data is in the host slot only (entry ptr -1) */
+    ORC_SW_MERGE = 2,  /* host data waiting to be fused into the device block */
+};
 
 /* ---------------------------------------------------------------- hashing */
 
@@ -135,6 +154,11 @@ void orc_scene_free(orc_scene *s)
     free(s->w);
     free(s->block_pos);
     free(s->alloc_order);
+    if (s->host)
+        for (int i = 0; i < s->nb + s->ne; ++i) free(s->host[i]);
+    free(s->host);
+    free(s->swap_state);
+    free(s->touch);
     free(s);
 }
 
@@ -169,8 +193,16 @@ static int take_block(orc_scene *s, int bx, int by, int bz)
     return ptr;
 }
 
+static void touch_entry(orc_scene *s, const orc_entry *e)
+{
+    if (s->swap_on) s->touch[e - s->entries] = s->frame;
+}
+
 /* Sec. 3.3 insertion: claim the bucket if it is free, otherwise walk to the
- * chain's end, reserve an excess entry and link it from the last entry. */
+ * chain's end, reserve an excess entry and link it from the last entry.  With
+ * swapping (Sec. 5), a key whose entry is swapped out (ptr -1) keeps that
+ * entry: it gets a fresh device block and waits for its host data to be
+ * fused in (ORC_SW_MERGE).  Every block met is stamped with the frame. */
 static void insert_if_missing(orc_scene *s, int bx, int by, int bz)
 {
     int idx = (int)orc_hash_index(bx, by, bz, (uint32_t)(s->nb - 1));
@@ -184,10 +216,22 @@ static void insert_if_missing(orc_scene *s, int bx, int by, int bz)
         e->y = (int16_t)by;
         e->z = (int16_t)bz;
         e->ptr = take_block(s, bx, by, bz);
+        touch_entry(s, e);
         return;
     }
     for (;;) {
-        if (e->x == bx && e->y == by && e->z == bz) return; /* present */
+        if (e->x == bx && e->y == by && e->z == bz) { /* present */
+            if (e->ptr == -1) {
+                if (s->block_top <= 0) {
+                    s->status |= ORC_ST_VBA_FULL;
+                    return;
+                }
+                e->ptr = take_block(s, bx, by, bz);
+                s->swap_state[e - s->entries] = ORC_SW_MERGE;
+            }
+            touch_entry(s, e);
+            return;
+        }
         if (e->offset < 1) break;
         e = &s->entries[s->nb + e->offset - 1];
     }
@@ -207,6 +251,7 @@ static void insert_if_missing(orc_scene *s, int bx, int by, int bz)
     n->offset = 0;
     n->ptr = take_block(s, bx, by, bz);
     e->offset = slot + 1;
+    touch_entry(s, n);
 }
 
 /* ------------------------------------------------------------ pose helpers */
@@ -302,6 +347,7 @@ int orc_allocate(orc_scene *s, const float *depth, int W, int H, const float int
     const float fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3];
     const float inv_b = (float)(1.0 / (8.0 * (double)s->voxel_size));
     const float mu = s->mu;
+    if (s->swap_on) ++s->frame;
     for (int v = 0; v < H; ++v) {
         for (int u = 0; u < W; ++u) {
             float d = depth[(size_t)v * W + u];
@@ -781,6 +827,186 @@ int orc_set_block(orc_scene *s, int bx, int by, int bz, const float *sdf, const 
         s->w[(size_t)ptr * ORC_BLOCK3 + i] = w[i];
     }
     return 0;
+}
+
+/* ---------------------------------------------------------------- swapping */
+
+/* Sec. 5 swapping.  Readings (the section describes the design, not every
+ * rule):
+ *   - the host map is a block store with one slot per hash entry (O2); a
+ *     swapped-out block keeps its entry, marked ptr -1, so a lookup that
+ *     meets it sees "not in device memory";
+ *   - swap-in is triggered by the allocation: when a segment meets a key
+ *     whose entry is swapped out, the entry gets a fresh device block at once
+ *     (the device goes on integrating live depth there, O3) and its host data
+ *     waits to be fused in (ORC_SW_MERGE);
+ *   - orc_swap_in fuses up to K waiting blocks into their device blocks, the
+ *     secondary integration of O3: per voxel the weighted mean
+ *     (W_d F_d + W_h F_h) / (W_d + W_h) with the weight min(W_d + W_h, max_w),
+ *     each operation rounded on its own, the device side first as in the
+ *     integration; a voxel the host never observed (W_h = 0) keeps the device
+ *     value, one the device has not observed yet (W_d = 0) takes the host
+ *     value unchanged;
+ *   - orc_swap_out moves up to K blocks to their host slots: blocks in device
+ *     memory with no host data waiting whose key no allocation segment has
+ *     met for `idle` allocations (the blocks the depth camera no longer
+ *     updates); their device blocks return to the free list;
+ *   - both take their K blocks in ascending bucket order and, within a
+ *     bucket's chain, ascending key (x, y, z as unsigned 16-bit fields, z
+ *     most significant): an order that depends only on the set of keys;
+ *   - transfers are bounded by K blocks per call (O1). */
+int orc_swap_enable(orc_scene *s, int k, int idle)
+{
+    if (s->swap_on || k <= 0 || idle < 0) return -1;
+    const int n = s->nb + s->ne;
+    s->swap_state = (uint8_t *)calloc((size_t)n, 1);
+    s->touch = (int32_t *)calloc((size_t)n, sizeof(int32_t));
+    s->host = (float **)calloc((size_t)n, sizeof(float *));
+    s->swap_k = k;
+    s->swap_idle = idle;
+    s->frame = 0;
+    s->swap_on = 1;
+    return 0;
+}
+
+static uint64_t packed_key(const orc_entry *e)
+{
+    return (uint64_t)(uint16_t)e->x | ((uint64_t)(uint16_t)e->y << 16) | ((uint64_t)(uint16_t)e->z << 32);
+}
+
+static int wants_out(const orc_scene *s, int idx)
+{
+    const orc_entry *e = &s->entries[idx];
+    return e->ptr >= 0 && s->swap_state[idx] == ORC_SW_DEVICE && s->frame - s->touch[idx] >= s->swap_idle;
+}
+
+static int wants_in(const orc_scene *s, int idx) { return s->swap_state[idx] == ORC_SW_MERGE; }
+
+/* Up to cap entry indices satisfying pred, bucket by bucket, each chain's in
+ * ascending key order. */
+static int select_entries(const orc_scene *s, int (*pred)(const orc_scene *, int), int32_t *out, int cap)
+{
+    int n = 0;
+    int32_t *chain = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s->ne + 1));
+    for (int h = 0; h < s->nb && n < cap; ++h) {
+        if (s->entries[h].ptr < -1) continue; /* bucket never used: no chain */
+        int m = 0, idx = h;
+        for (;;) {
+            if (pred(s, idx)) {
+                int j = m++;
+                while (j > 0 && packed_key(&s->entries[chain[j - 1]]) > packed_key(&s->entries[idx])) {
+                    chain[j] = chain[j - 1];
+                    --j;
+                }
+                chain[j] = idx;
+            }
+            if (s->entries[idx].offset < 1) break;
+            idx = s->nb + s->entries[idx].offset - 1;
+        }
+        for (int j = 0; j < m && n < cap; ++j) out[n++] = chain[j];
+    }
+    free(chain);
+    return n;
+}
+
+/* Moves up to K blocks to the host; returns how many. */
+int orc_swap_out(orc_scene *s)
+{
+    if (!s->swap_on) return -1;
+    int32_t *sel = (int32_t *)malloc(sizeof(int32_t) * (size_t)s->swap_k);
+    const int n = select_entries(s, wants_out, sel, s->swap_k);
+    for (int j = 0; j < n; ++j) {
+        const int idx = sel[j];
+        orc_entry *e = &s->entries[idx];
+        const int ptr = e->ptr;
+        if (!s->host[idx]) s->host[idx] = (float *)malloc(sizeof(float) * 2 * ORC_BLOCK3);
+        memcpy(s->host[idx], &s->sdf[(size_t)ptr * ORC_BLOCK3], sizeof(float) * ORC_BLOCK3);
+        memcpy(s->host[idx] + ORC_BLOCK3, &s->w[(size_t)ptr * ORC_BLOCK3], sizeof(float) * ORC_BLOCK3);
+        e->ptr = -1;
+        s->swap_state[idx] = ORC_SW_HOST;
+        /* the block leaves the allocated list and returns to the free stack */
+        int k = 0;
+        while (k < s->n_alloc && s->alloc_order[k] != ptr) ++k;
+        for (; k + 1 < s->n_alloc; ++k) s->alloc_order[k] = s->alloc_order[k + 1];
+        --s->n_alloc;
+        s->block_free[s->block_top++] = ptr;
+    }
+    free(sel);
+    s->swapped_out += n;
+    return n;
+}
+
+/* Secondary fusion of one voxel: device (F, W) and host (Fh, Wh). */
+static void fuse_voxel(float *F, float *W, float Fh, float Wh, float max_w)
+{
+    if (!(Wh > 0.0f)) return;
+    if (!(*W > 0.0f)) {
+        *F = Fh;
+        *W = Wh;
+        return;
+    }
+    float num = *W * *F + Wh * Fh;
+    float den = *W + Wh;
+    *F = num / den;
+    *W = den < max_w ? den : max_w;
+}
+
+/* Fuses up to K waiting host blocks into their device blocks; returns how many. */
+int orc_swap_in(orc_scene *s)
+{
+    if (!s->swap_on) return -1;
+    int32_t *sel = (int32_t *)malloc(sizeof(int32_t) * (size_t)s->swap_k);
+    const int n = select_entries(s, wants_in, sel, s->swap_k);
+    const float max_w = (float)s->max_w;
+    for (int j = 0; j < n; ++j) {
+        const int idx = sel[j];
+        const int ptr = s->entries[idx].ptr;
+        const float *h = s->host[idx];
+        for (int i = 0; i < ORC_BLOCK3; ++i)
+            fuse_voxel(&s->sdf[(size_t)ptr * ORC_BLOCK3 + i], &s->w[(size_t)ptr * ORC_BLOCK3 + i], h[i],
+                       h[ORC_BLOCK3 + i], max_w);
+        s->swap_state[idx] = ORC_SW_DEVICE;
+    }
+    free(sel);
+    s->swapped_in += n;
+    return n;
+}
+
+/* out: blocks with host data (swapped out or waiting), swapped-out blocks,
+ * blocks waiting, blocks moved in, blocks moved out. */
+void orc_swap_counters(const orc_scene *s, long long out[5])
+{
+    long long host = 0, waiting = 0;
+    for (int i = 0; s->swap_on && i < s->nb + s->ne; ++i) {
+        host += s->swap_state[i] == ORC_SW_HOST;
+        waiting += s->swap_state[i] == ORC_SW_MERGE;
+    }
+    out[0] = host + waiting;
+    out[1] = host;
+    out[2] = waiting;
+    out[3] = s->swapped_in;
+    out[4] = s->swapped_out;
+}
+
+/* The host slots of the blocks that have host data (swapped out or waiting):
+ * coords, sdf, weights and state (ORC_SW_HOST or ORC_SW_MERGE), in entry
+ * order; returns the count (all of it when cap is 0 and the arrays NULL). */
+int orc_swap_export_host(const orc_scene *s, int16_t *coords, float *sdf, float *w, int32_t *state, int cap)
+{
+    int n = 0;
+    for (int i = 0; s->swap_on && i < s->nb + s->ne; ++i) {
+        if (s->swap_state[i] == ORC_SW_DEVICE) continue;
+        if (n < cap) {
+            coords[3 * n] = s->entries[i].x;
+            coords[3 * n + 1] = s->entries[i].y;
+            coords[3 * n + 2] = s->entries[i].z;
+            memcpy(&sdf[(size_t)n * ORC_BLOCK3], s->host[i], sizeof(float) * ORC_BLOCK3);
+            memcpy(&w[(size_t)n * ORC_BLOCK3], s->host[i] + ORC_BLOCK3, sizeof(float) * ORC_BLOCK3);
+            state[n] = s->swap_state[i];
+        }
+        ++n;
+    }
+    return n;
 }
 
 /* ---------------------------------------------------------------- tracking */

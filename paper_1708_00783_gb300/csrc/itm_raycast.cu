@@ -72,7 +72,7 @@ __global__ void __launch_bounds__(256) range_kernel(SceneDev s, Mat34 M, Intr in
 // last.  With write_order each finished tile is appended to the queue of its
 // cost class for the next raycast.  hdr_w[0] is this raycast's tile counter.
 template <int MODE>
-__global__ void __launch_bounds__(256) raycast_dynamic_kernel(SceneDev s, Intr in, Mat34 T, float4 *__restrict__ vtx,
+__global__ void __launch_bounds__(256, 4) raycast_dynamic_kernel(SceneDev s, Intr in, Mat34 T, float4 *__restrict__ vtx,
                                                               float4 *__restrict__ nrm, int max_iter, float tB_m,
                                                               float inv_sv, const uint32_t *__restrict__ rmin,
                                                               const uint32_t *__restrict__ rmax, int tiles_x,
