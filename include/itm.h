@@ -478,6 +478,70 @@ int itm_frame_blocks_noalloc(const float *depth_dev, const itm_intrinsics *intr,
                              float voxel_size, float mu, float z_min, float z_max, int16_t *coords_dev,
                              int cap, int32_t *count_dev, itm_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Sec. 5 swapping: only the active part of the map stays in device memory;
+ * the rest lives in a host block store with one slot per hash entry (the
+ * paper's objective O2: a hash entry index is the host address).  A
+ * swapped-out block keeps its hash entry with ptr -1 (Sec. 3.2).  Per frame:
+ * itm_allocate (a segment that meets a swapped-out key gives its entry a
+ * fresh device block and marks the host data as waiting), itm_swap_in,
+ * itm_integrate, itm_raycast, itm_swap_out -- the order of the paper's
+ * swapping pipeline.  itm_process_frame* do not swap; batches
+ * (itm_batch_run) reject scenes with swapping on.
+ *
+ * The store is pinned host memory mapped into the device: the swap kernels
+ * read and write a block's slot directly, so the host does no per-block work
+ * and no transfer buffers are staged; each call moves at most
+ * transfer_blocks blocks (objective O1).  Blocks are taken bucket by bucket
+ * and, within a chain, in ascending key order (x, y, z as unsigned 16-bit
+ * fields, z most significant), an order fixed by the set of keys.
+ * ---------------------------------------------------------------------- */
+
+/* Turns swapping on: allocates the host store ((num_buckets + num_excess) x
+ * 512 x (4 + weight bytes), pinned and mapped) and the device state.
+ * transfer_blocks (1 .. 2^24): blocks moved per call at most.  idle_frames
+ * (>= 0): a block leaves the device once no allocation segment has met it
+ * for that many allocations (0: every block without waiting host data is a
+ * candidate).  ITM_ERR_ARG when swapping is already on or an argument is out
+ * of range, ITM_ERR_CUDA when the memory cannot be had.  Freed with the
+ * scene; itm_scene_reset clears it. */
+int itm_swap_enable(itm_scene *scene, int transfer_blocks, int idle_frames);
+
+/* The secondary integration of Sec. 5: up to transfer_blocks blocks whose
+ * host data is waiting are fused into their device blocks, per voxel
+ * F = (W_d F_d + W_h F_h) / (W_d + W_h), W = min(W_d + W_h, max_w), each
+ * operation rounded on its own (a voxel the host never observed keeps the
+ * device value; one the device has not observed takes the host value).
+ * Asynchronous on stream; ITM_ERR_ARG when swapping is off. */
+int itm_swap_in(itm_scene *scene, itm_stream stream);
+
+/* Moves up to transfer_blocks blocks to their host slots: blocks in device
+ * memory with no host data waiting that no allocation segment met in the
+ * last idle_frames allocations.  Their entries keep their keys with ptr -1,
+ * their device blocks are reset (sdf 1, weight 0) and return to the free
+ * list.  Asynchronous on stream; ITM_ERR_ARG when swapping is off. */
+int itm_swap_out(itm_scene *scene, itm_stream stream);
+
+typedef struct {
+    int64_t host_data;    /* entries with host data (swapped out or waiting) */
+    int64_t swapped_out;  /* entries whose block is in the host store only */
+    int64_t waiting;      /* entries with a device block and host data to fuse */
+    int64_t moved_in;     /* blocks fused in since swapping was enabled */
+    int64_t moved_out;    /* blocks moved to the host since swapping was enabled */
+} itm_swap_counters;
+
+/* Waits for the scene's last stream; ITM_ERR_ARG when swapping is off. */
+int itm_swap_get_counters(itm_scene *scene, itm_swap_counters *out);
+
+/* The host slots of the entries with host data, in entry order: coords
+ * (host int16[cap][3]), sdf (host float[cap][512]), weights (host
+ * uint8[cap][512] or float[cap][512] by weight_mode) and state (host
+ * int32[cap]: 1 swapped out, 2 waiting).  *n receives the count;
+ * ITM_ERR_TOO_LARGE when it exceeds cap (cap 0 with null arrays asks for the
+ * count).  Waits for the scene's last stream. */
+int itm_swap_export_host(itm_scene *scene, int16_t *coords_host, float *sdf_host, void *w_host,
+                         int32_t *state_host, int cap, int *n);
+
 #ifdef __cplusplus
 }
 #endif

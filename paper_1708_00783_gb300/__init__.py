@@ -70,6 +70,14 @@ class itm_stats(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class itm_swap_counters(ctypes.Structure):
+    _fields_ = [("host_data", ctypes.c_int64), ("swapped_out", ctypes.c_int64), ("waiting", ctypes.c_int64),
+                ("moved_in", ctypes.c_int64), ("moved_out", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 EXPORTED = [
     "itm_scene_create", "itm_scene_destroy", "itm_scene_reset", "itm_allocate", "itm_integrate",
     "itm_integrate_weighted", "itm_raycast", "itm_process_frame", "itm_depth_u16_to_f32",
@@ -77,7 +85,8 @@ EXPORTED = [
     "itm_scene_import", "itm_hash_index", "itm_version", "itm_frame_blocks_noalloc", "itm_raycast_range",
     "itm_mlp_pack", "itm_conf_weights", "itm_conf_features", "itm_mlp_loss_grad", "itm_mlp_adam",
     "itm_batch_create", "itm_batch_destroy", "itm_batch_run", "itm_batch_set_tuning", "itm_batch_get_tuning",
-    "itm_batch_set_graph",
+    "itm_batch_set_graph", "itm_swap_enable", "itm_swap_in", "itm_swap_out", "itm_swap_get_counters",
+    "itm_swap_export_host",
 ]
 
 
@@ -128,6 +137,11 @@ def _load():
         "itm_batch_set_tuning": (I, [P, ctypes.POINTER(I), I]),
         "itm_batch_get_tuning": (I, [P, ctypes.POINTER(I), I]),
         "itm_batch_set_graph": (I, [P, I]),
+        "itm_swap_enable": (I, [P, I, I]),
+        "itm_swap_in": (I, [P, P]),
+        "itm_swap_out": (I, [P, P]),
+        "itm_swap_get_counters": (I, [P, ctypes.POINTER(itm_swap_counters)]),
+        "itm_swap_export_host": (I, [P, P, P, P, P, I, ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -452,6 +466,44 @@ def itm_batch_set_graph(batch, use_graph):
 
 # ------------------------------------------------------------ convenience
 
+# ------------------------------------------------------------ Sec. 5 swapping
+
+SW_HOST, SW_MERGE = 1, 2
+
+
+def itm_swap_enable(scene, transfer_blocks, idle_frames=1):
+    _check(_lib.itm_swap_enable(scene, int(transfer_blocks), int(idle_frames)), "itm_swap_enable")
+
+
+def itm_swap_in(scene, stream=None):
+    _check(_lib.itm_swap_in(scene, _stream(stream)), "itm_swap_in")
+
+
+def itm_swap_out(scene, stream=None):
+    _check(_lib.itm_swap_out(scene, _stream(stream)), "itm_swap_out")
+
+
+def itm_swap_get_counters(scene) -> dict:
+    c = itm_swap_counters()
+    _check(_lib.itm_swap_get_counters(scene, ctypes.byref(c)), "itm_swap_get_counters")
+    return c.as_dict()
+
+
+def itm_swap_export_host(scene, weight_mode=0):
+    """(coords int16 [n,3], sdf float32 [n,512], w float32 [n,512], state
+    int32 [n]) of the host slots of the entries with host data."""
+    n = ctypes.c_int(0)
+    _check(_lib.itm_swap_export_host(scene, None, None, None, None, 0, ctypes.byref(n)), "itm_swap_export_host")
+    cnt = n.value
+    coords = np.zeros((max(cnt, 1), 3), dtype=np.int16)
+    sdf = np.zeros((max(cnt, 1), 512), dtype=np.float32)
+    w = np.zeros((max(cnt, 1), 512), dtype=np.uint8 if weight_mode == 0 else np.float32)
+    st = np.zeros(max(cnt, 1), dtype=np.int32)
+    _check(_lib.itm_swap_export_host(scene, coords.ctypes.data, sdf.ctypes.data, w.ctypes.data, st.ctypes.data,
+                                     cnt, ctypes.byref(n)), "itm_swap_export_host")
+    return coords[:cnt], sdf[:cnt], w[:cnt].astype(np.float32), st[:cnt]
+
+
 class Scene:
     """Owning wrapper of an itm_scene handle."""
 
@@ -499,6 +551,21 @@ class Scene:
 
     def export(self, with_voxels=True):
         return itm_scene_export(self.handle, with_voxels)
+
+    def swap_enable(self, transfer_blocks, idle_frames=1):
+        itm_swap_enable(self.handle, transfer_blocks, idle_frames)
+
+    def swap_in(self, stream=None):
+        itm_swap_in(self.handle, stream)
+
+    def swap_out(self, stream=None):
+        itm_swap_out(self.handle, stream)
+
+    def swap_counters(self) -> dict:
+        return itm_swap_get_counters(self.handle)
+
+    def swap_export_host(self):
+        return itm_swap_export_host(self.handle, self.params["weight_mode"])
 
     def export_table(self):
         return itm_scene_export_table(self.handle, self.params["num_buckets"], self.params["num_excess"])

@@ -41,6 +41,7 @@ SOURCES = {
     "itm_conf.cu": [],
     "itm_batch.cu": ["-fmad=false"],
     "itm_combined.cu": ["-fmad=false"],
+    "itm_swap.cu": ["-fmad=false"],
     "itm_track.cu": ["-fmad=false"],
     "itm_mesh.cu": ["-fmad=false"],
 }

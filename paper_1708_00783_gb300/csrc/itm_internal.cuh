@@ -12,6 +12,11 @@
 //   block_free  int32[nv]           free block list, handed out front to back
 //   excess_free int32[ne]           free excess slots, handed out front to back
 //   ctr         Counters            device counters and the sticky status word
+//   swap_state  uint8[nb + ne]      Sec. 5 swapping (itm_swap_enable): kSw* per entry
+//   touch       int32[nv]           last allocation whose segments met the block (-1: freed
+//                                   by the running swap-out)
+//   host store  pinned host memory mapped into the device, one slot per entry:
+//               float[nb + ne][512] sdf and uint8 / float [nb + ne][512] weights
 #pragma once
 
 #include <cuda_runtime.h>
@@ -37,6 +42,11 @@ constexpr int kIcpWorkDoubles = ITM_ICP_WORK_DOUBLES;
 constexpr int kIcpMaxPartials = ITM_ICP_WORK_DOUBLES / ITM_ICP_SUMS - 1;
 constexpr int kTrackMaxLevels = ITM_TRACK_MAX_LEVELS;
 constexpr unsigned kFull = 0xffffffffu;
+
+// Sec. 5 swap state of a hash entry
+constexpr uint8_t kSwDevice = 0;  // current data in the device block (or none)
+constexpr uint8_t kSwHost = 1;    // swapped out: data in the host slot only, entry ptr -1
+constexpr uint8_t kSwMerge = 2;   // host data waiting to be fused into the device block
 
 // Sec. 3.2 hash entry.  Bytes 0..7 (x, y, z, flag) form the packed block key
 // compared and claimed as one 64-bit word; flag = 1 marks an entry that holds
@@ -87,6 +97,10 @@ struct SceneDev {
     // class a list of up to kOrderMaxTiles tiles
     int32_t *tile_q_hdr;
     int32_t *tile_q_list;
+    // Sec. 5 swapping: null while swapping is off
+    uint8_t *swap_state;
+    int32_t *touch;
+    int swap_frame;  // allocations since swapping was enabled
     int nb, ne, nv;
     int ovf_cap;
     float voxel_size, mu, z_min, z_max;
@@ -227,6 +241,11 @@ struct itm_scene {
     // tiles_y image ({0, 0}: none yet); the next raycast writes side order_side
     int order_dims[2];
     int order_side;
+    // Sec. 5 swapping (itm_swap_enable): the host store (pinned, mapped) and
+    // the device scratch of the selection
+    void *host_sdf, *host_w;
+    void *swap_scratch;
+    int swap_k, swap_idle;
 };
 
 // Host helpers implemented in itm_scene.cu.
@@ -250,6 +269,10 @@ cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 
                                  cudaStream_t st);
 bool range_fits(const Intr &in);
 cudaError_t launch_mesh(const SceneDev &s, float *out, long long cap, unsigned long long *counter, cudaStream_t st);
+// Sec. 5 swapping state of a scene: freed by itm_scene_destroy, cleared by
+// itm_scene_reset (itm_swap.cu)
+void swap_free(itm_scene *sc);
+cudaError_t swap_reset(itm_scene *sc, cudaStream_t st);
 cudaError_t launch_depth_halve(const float *in, int W, int H, float *out, cudaStream_t st);
 cudaError_t launch_icp_reduce(const float *depth, const Intr &in, const Mat34 &T_g, const float4 *V, const float4 *N,
                               const Intr &ref, const Mat34 &M_ref, float dist_thresh, double *work, cudaStream_t st);

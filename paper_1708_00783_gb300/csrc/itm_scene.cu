@@ -5,6 +5,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <vector>
 
 #include "itm_internal.cuh"
@@ -100,6 +101,19 @@ static void free_dev(SceneDev &d)
     memset(&d, 0, sizeof(d));
 }
 
+// Copies blocks ptrs[0..n) (sdf, and weights as float) to out[j].
+__global__ void gather_blocks_kernel(SceneDev s, const int32_t *__restrict__ ptrs, int n, float *__restrict__ out_sdf,
+                                     float *__restrict__ out_w)
+{
+    for (int j = blockIdx.x; j < n; j += gridDim.x) {
+        const size_t src = (size_t)ptrs[j] * kBlockVoxels, dst = (size_t)j * kBlockVoxels;
+        for (int i = threadIdx.x; i < kBlockVoxels; i += blockDim.x) {
+            out_sdf[dst + i] = s.sdf[src + i];
+            out_w[dst + i] = s.w8 ? (float)s.w8[src + i] : s.w32[src + i];
+        }
+    }
+}
+
 static const char kVersion[] = "itm-gb300 0.1 (sm_103a)";
 
 }  // namespace itm
@@ -175,6 +189,7 @@ int itm_scene_destroy(itm_scene *sc)
 {
     if (!sc) return ITM_ERR_ARG;
     cudaDeviceSynchronize();
+    swap_free(sc);
     free_dev(sc->d);
     free(sc);
     return ITM_OK;
@@ -187,7 +202,9 @@ int itm_scene_reset(itm_scene *sc, itm_stream stream)
     sc->alloc_epoch++;
     cudaStream_t st = (cudaStream_t)stream;
     sc->last_stream = st;
-    return check_cuda(launch_reset(sc->d, st));
+    cudaError_t e = launch_reset(sc->d, st);
+    if (e == cudaSuccess) e = swap_reset(sc, st);
+    return check_cuda(e);
 }
 
 static int allocate_impl(itm_scene *sc, const float *depth_dev, const uint16_t *raw_dev, const itm_intrinsics *intr,
@@ -202,6 +219,7 @@ static int allocate_impl(itm_scene *sc, const float *depth_dev, const uint16_t *
     const Intr in = to_intr(intr);
     const bool with_range = range_fits(in);
     sc->alloc_epoch++;
+    if (sc->d.swap_state) sc->d.swap_frame++;  // Sec. 5: the blocks this allocation meets are stamped with it
     const int r = check_cuda(launch_allocate(sc->d, depth_dev, in, T, M, with_range, st, raw_dev));
     if (r == ITM_OK && with_range) {
         // the range tiles now hold the range of a raycast from this pose
@@ -531,56 +549,59 @@ int itm_scene_export(itm_scene *sc, int16_t *coords_host, float *sdf_host, float
     itm_stats st;
     int r = itm_scene_stats(sc, &st);
     if (r != ITM_OK) return r;
+    // the allocated blocks are block_free[0 .. allocated_blocks), in the
+    // order they were handed out (swap-outs fill their gaps from the end)
     const int total = st.allocated_blocks;
-    std::vector<short4> pos((size_t)(total > 0 ? total : 1));
+    const int nv = sc->d.nv;
     std::vector<int32_t> order((size_t)(total > 0 ? total : 1));
+    std::vector<short4> pos((size_t)(nv > 0 ? nv : 1));
     cudaError_t e = cudaSuccess;
     if (total > 0) {
         e = cudaMemcpy(order.data(), sc->d.block_free, sizeof(int32_t) * total, cudaMemcpyDeviceToHost);
-        if (e == cudaSuccess)
-            e = cudaMemcpy(pos.data(), sc->d.block_pos, sizeof(short4) * total, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpy(pos.data(), sc->d.block_pos, sizeof(short4) * nv, cudaMemcpyDeviceToHost);
     }
     if (e != cudaSuccess) return ITM_ERR_CUDA;
-    for (int i = 0; i < total; ++i)
-        if (order[i] != i) return ITM_ERR_ARG;  // the front-to-back invariant above
-    int k = 0;
-    std::vector<int> keep;
+    std::vector<int32_t> keep;
     keep.reserve(total);
-    for (int i = 0; i < total; ++i)
-        if (pos[i].w) keep.push_back(i);
+    for (int i = 0; i < total; ++i) {
+        if (order[i] < 0 || order[i] >= nv) return ITM_ERR_ARG;  // not a block index: a corrupted list
+        if (pos[order[i]].w) keep.push_back(order[i]);
+    }
     const int m = (int)keep.size();
     *n = m;
     const int cnt = m < cap ? m : cap;
     std::vector<float> sdf, wf;
-    std::vector<uint8_t> w8;
     if (cnt > 0 && (sdf_host || w_host)) {
-        const size_t nvox = (size_t)total * kBlockVoxels;
-        if (sdf_host) {
+        // gather the kept blocks on the device, then one copy each
+        const size_t nvox = (size_t)cnt * kBlockVoxels;
+        int32_t *ptrs = nullptr;
+        float *g_sdf = nullptr, *g_w = nullptr;
+        e = cudaMalloc((void **)&ptrs, sizeof(int32_t) * cnt);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&g_sdf, sizeof(float) * nvox);
+        if (e == cudaSuccess) e = cudaMalloc((void **)&g_w, sizeof(float) * nvox);
+        if (e == cudaSuccess) e = cudaMemcpy(ptrs, keep.data(), sizeof(int32_t) * cnt, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) {
+            gather_blocks_kernel<<<std::min(cnt, 4096), 128>>>(sc->d, ptrs, cnt, g_sdf, g_w);
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) {
             sdf.resize(nvox);
-            e = cudaMemcpy(sdf.data(), sc->d.sdf, sizeof(float) * nvox, cudaMemcpyDeviceToHost);
+            wf.resize(nvox);
+            e = cudaMemcpy(sdf.data(), g_sdf, sizeof(float) * nvox, cudaMemcpyDeviceToHost);
+            if (e == cudaSuccess) e = cudaMemcpy(wf.data(), g_w, sizeof(float) * nvox, cudaMemcpyDeviceToHost);
         }
-        if (e == cudaSuccess && w_host) {
-            if (sc->d.weight_mode == 0) {
-                w8.resize(nvox);
-                e = cudaMemcpy(w8.data(), sc->d.w8, nvox, cudaMemcpyDeviceToHost);
-            } else {
-                wf.resize(nvox);
-                e = cudaMemcpy(wf.data(), sc->d.w32, sizeof(float) * nvox, cudaMemcpyDeviceToHost);
-            }
-        }
+        if (ptrs) cudaFree(ptrs);
+        if (g_sdf) cudaFree(g_sdf);
+        if (g_w) cudaFree(g_w);
         if (e != cudaSuccess) return ITM_ERR_CUDA;
     }
-    for (k = 0; k < cnt; ++k) {
-        const int b = keep[k];
-        coords_host[3 * k + 0] = pos[b].x;
-        coords_host[3 * k + 1] = pos[b].y;
-        coords_host[3 * k + 2] = pos[b].z;
-        if (sdf_host) memcpy(&sdf_host[(size_t)k * kBlockVoxels], &sdf[(size_t)b * kBlockVoxels], sizeof(float) * kBlockVoxels);
-        if (w_host) {
-            for (int i = 0; i < kBlockVoxels; ++i)
-                w_host[(size_t)k * kBlockVoxels + i] = sc->d.weight_mode == 0 ? (float)w8[(size_t)b * kBlockVoxels + i]
-                                                                              : wf[(size_t)b * kBlockVoxels + i];
-        }
+    for (int k = 0; k < cnt; ++k) {
+        const short4 b = pos[keep[k]];
+        coords_host[3 * k + 0] = b.x;
+        coords_host[3 * k + 1] = b.y;
+        coords_host[3 * k + 2] = b.z;
+        if (sdf_host) memcpy(&sdf_host[(size_t)k * kBlockVoxels], &sdf[(size_t)k * kBlockVoxels], sizeof(float) * kBlockVoxels);
+        if (w_host) memcpy(&w_host[(size_t)k * kBlockVoxels], &wf[(size_t)k * kBlockVoxels], sizeof(float) * kBlockVoxels);
     }
     return ITM_OK;
 }
@@ -656,6 +677,7 @@ int itm_scene_import(itm_scene *sc, const int16_t *coords_host, const float *sdf
     sc->alloc_epoch++;
     cudaError_t e = cudaStreamSynchronize(sc->last_stream);
     if (e == cudaSuccess) e = launch_reset(d, 0);
+    if (e == cudaSuccess) e = swap_reset(sc, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e == cudaSuccess)
         e = cudaMemcpy(d.entries, E.data(), sizeof(Entry) * E.size(), cudaMemcpyHostToDevice);
