@@ -471,6 +471,71 @@ def run_mesh_section(itm, torch, dev, stream, scene, flush, blocks, reps=5):
             "algorithmic_bytes": alg, "achieved_gbs": alg / (t / 1000.0) / 1e9}
 
 
+SWAP_BLOCKS = 1 << 14   # device block array of the swapping run: about half of the room's map
+SWAP_K = 8192            # blocks moved per swap call at most
+SWAP_IDLE = 1            # allocations without a segment meeting a block before it leaves the device
+
+
+def run_swap_section(itm, torch, stream, params, raw_dev, poses, ci, depth, vtx, nrm, flush, n_frames, warmup):
+    """Sec. 5 swapping on the room trajectory with a device block array of
+    2^14 blocks, about half of the map the trajectory builds (without swapping
+    the array runs out).  Per frame: allocation, swap-in (secondary fusion),
+    integration, raycast, swap-out, each timed with CUDA events; L2 flushed
+    between frames.  Host bytes: a block's 512 sdf floats and 512 weight
+    bytes cross the host link once per move."""
+    sc = itm.Scene(**dict(params, num_blocks=SWAP_BLOCKS))
+    sc.swap_enable(SWAP_K, SWAP_IDLE)
+
+    def frame(k, e=None):
+        calls = (lambda: itm.itm_allocate_u16(sc.handle, raw_dev[k], depth, ci, poses[k], stream),
+                 lambda: sc.swap_in(stream),
+                 lambda: itm.itm_integrate(sc.handle, depth, ci, poses[k], stream),
+                 lambda: itm.itm_raycast(sc.handle, ci, poses[k], vtx, nrm, stream),
+                 lambda: sc.swap_out(stream))
+        for j, c in enumerate(calls):
+            if e is not None:
+                e[j].record(stream)
+            c()
+        if e is not None:
+            e[5].record(stream)
+
+    ks = sorted(raw_dev)  # the frames resident for the timed region
+    warmup = min(warmup, len(ks) - 1)
+    for k in ks[:warmup]:
+        frame(k)
+    torch.cuda.synchronize()
+    c0 = sc.swap_counters()
+    timed = ks[warmup:]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in timed]
+    for i, k in enumerate(timed):
+        frame(k, ev[i])
+        flush.zero_()
+    torch.cuda.synchronize()
+    c1 = sc.swap_counters()
+    st = sc.stats()
+    stage = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(5)] for e in ev])
+    names = ["u16_to_f32_and_allocate", "swap_in", "integrate", "raycast", "swap_out"]
+    n = len(timed)
+    moved_in, moved_out = c1["moved_in"] - c0["moved_in"], c1["moved_out"] - c0["moved_out"]
+    block_host_bytes = 512 * (4 + (1 if params.get("weight_mode", 0) == 0 else 4))
+    t_in, t_out = float(stage[:, 1].sum()), float(stage[:, 4].sum())
+    return {
+        "workload": "the room trajectory (frames %d..%d timed) with a device block array of %d blocks, %d blocks "
+                    "moved per call at most, blocks leave after %d allocations without a segment meeting them; "
+                    "host store pinned and mapped into the device" % (timed[0], timed[-1], SWAP_BLOCKS, SWAP_K,
+                                                                        SWAP_IDLE),
+        "status": st["status"],
+        "frames_per_s": n / (float(stage.sum()) / 1000.0),
+        "stage_ms_mean": {nm: float(stage[:, j].mean()) for j, nm in enumerate(names)},
+        "device_blocks_end": st["allocated_blocks"],
+        "map_blocks_end": st["allocated_blocks"] + c1["swapped_out"],
+        "blocks_in_per_frame": moved_in / n,
+        "blocks_out_per_frame": moved_out / n,
+        "host_link_gbs_swap_in": moved_in * block_host_bytes / (t_in / 1000.0) / 1e9 if t_in > 0 else None,
+        "host_link_gbs_swap_out": moved_out * block_host_bytes / (t_out / 1000.0) / 1e9 if t_out > 0 else None,
+    }
+
+
 TRACK_ITERS = [10, 5, 4]          # pyramid level 0 (640x480), 1, 2
 TRACK_THRESH = [0.05, 0.1, 0.2]   # outlier distance per level, metres
 
@@ -724,6 +789,10 @@ def run_ours(args, world, rank, local):
     mesh_rep = None
     if extra and args.mesh:
         mesh_rep = run_mesh_section(itm, torch, dev, stream, scene, flush, st1["allocated_blocks"])
+    swap_rep = None
+    if extra and args.swap:
+        swap_rep = run_swap_section(itm, torch, stream, w.params, raw_dev, poses, ci, depth, vtx, nrm, flush,
+                                    n_frames, args.warmup)
     tracking_rep = None
     if extra and args.tracking:
         tracking_rep = run_tracking_section(itm, torch, dev, stream, scene, raw_dev, poses, ci, depth, vtx, nrm,
@@ -854,6 +923,7 @@ def run_ours(args, world, rank, local):
         "learned": learned_rep,
         "tracking": tracking_rep,
         "mesh": mesh_rep,
+        "swapping": swap_rep,
     }
     print(json.dumps(line), flush=True)
 
@@ -870,9 +940,10 @@ def main(argv=None):
     ap.add_argument("--no-learned", dest="learned", action="store_false")
     ap.add_argument("--no-tracking", dest="tracking", action="store_false")
     ap.add_argument("--no-mesh", dest="mesh", action="store_false")
+    ap.add_argument("--no-swap", dest="swap", action="store_false")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="kinect",
                     help="configuration of the per-frame loop (default: the 640x480 / 5 mm room the metric is "
-                         "quoted on); the batched, learned, tracking and mesh sections run with the default only")
+                         "quoted on); the batched, learned, tracking, mesh and swapping sections run with the default only")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
