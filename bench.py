@@ -471,15 +471,15 @@ def run_mesh_section(itm, torch, dev, stream, scene, flush, blocks, reps=5):
             "algorithmic_bytes": alg, "achieved_gbs": alg / (t / 1000.0) / 1e9}
 
 
-SWAP_BLOCKS = 1 << 14   # device block array of the swapping run: about half of the room's map
+SWAP_BLOCKS = 20480     # device block array of the swapping run: about two thirds of the room's map
 SWAP_K = 8192            # blocks moved per swap call at most
 SWAP_IDLE = 1            # allocations without a segment meeting a block before it leaves the device
 
 
 def run_swap_section(itm, torch, stream, params, raw_dev, poses, ci, depth, vtx, nrm, flush, n_frames, warmup):
     """Sec. 5 swapping on the room trajectory with a device block array of
-    2^14 blocks, about half of the map the trajectory builds (without swapping
-    the array runs out).  Per frame: allocation, swap-in (secondary fusion),
+    20480 blocks, about two thirds of the 29.6k-block map the trajectory
+    builds (without swapping the array runs out).  Per frame: allocation, swap-in (secondary fusion),
     integration, raycast, swap-out, each timed with CUDA events; L2 flushed
     between frames.  Host bytes: a block's 512 sdf floats and 512 weight
     bytes cross the host link once per move."""

@@ -21,11 +21,15 @@
 //     within a chain, in ascending key order: an order fixed by the set of
 //     keys alone, independent of which thread won which atomic.
 //
-// Selection (both directions): swap_count_kernel counts the candidates of
-// each chunk of 1024 buckets; swap_select_kernel gives each chunk its offset
-// (the counts of the chunks before it), ranks its buckets with block scans in
-// bucket order and the candidates of a chain by key, and writes the entry
-// indices of ranks < K.  Eviction then frees the blocks, and a two-kernel
+// Selection (both directions): candidates are blocks in device memory, so
+// swap_scan_kernel visits the allocated blocks (the prefix of the free list),
+// finds each one's entry and lists the candidates.  When there are at most K,
+// all of them move and their order does not matter: that list is the
+// selection.  Only when there are more do the ordered kernels run:
+// swap_count_kernel counts the candidates of each chunk of 1024 buckets;
+// swap_select_kernel gives each chunk its offset (the counts of the chunks
+// before it), ranks its buckets with block scans in bucket order and the
+// candidates of a chain by key, and writes the entry indices of ranks < K.  Eviction then frees the blocks, and a two-kernel
 // compaction swaps the freed blocks of the allocated prefix of the free list
 // with blocks still in use from its end, so the prefix stays "the allocated
 // blocks".
@@ -60,7 +64,8 @@ struct SwapDev {
     float *host_w32;     // weight mode 1
     int32_t *chunk;      // per bucket chunk: candidates
     int32_t *sel;        // [k] selected entry indices, in order
-    int32_t *hdr;        // [0] selected, [1] holes, [2] movers, [3] allocated prefix length, [4] freed
+    int32_t *hdr;        // [0] selected, [1] holes, [2] movers, [3] allocated prefix length, [4] freed,
+                         // [5] candidates found by the scan of the allocated blocks
     int32_t *holes;      // [k] free-list positions
     int32_t *movers;     // [k]
     unsigned long long *moved;  // [0] fused in, [1] moved out (cumulative)
@@ -179,9 +184,63 @@ __device__ void emit_bucket(const SceneDev &s, const SwapDev &w, int h, int firs
     }
 }
 
+// The entry holding block ptr (coordinates b): the chain element with b's key
+// and that ptr, or -1.
+__device__ __forceinline__ int entry_of(const SceneDev &s, short4 b, int ptr)
+{
+    const unsigned long long key = pack_key(b.x, b.y, b.z);
+    const int4 *E = reinterpret_cast<const int4 *>(s.entries);
+    int idx = (int)hash_bucket(b.x, b.y, b.z, (uint32_t)(s.nb - 1));
+    for (int guard = 0; guard <= s.ne; ++guard) {
+        const int4 e = __ldcg(&E[idx]);
+        if (entry_key(e) == key) return e.w == ptr ? idx : -1;
+        if (e.z < 1 || !ITM_IN_BOUNDS(s, e.z - 1 < s.ne)) return -1;
+        idx = s.nb + e.z - 1;
+    }
+    return -1;
+}
+
+// Candidates among the allocated blocks: hdr[5] counts them, the first K
+// found are listed.
+template <bool OUT>
+__global__ void __launch_bounds__(256) swap_scan_kernel(SceneDev s, SwapDev w)
+{
+    const int head = min(__ldcg(&s.ctr->block_head), s.nv);
+    const int stride = gridDim.x * blockDim.x;
+    for (int p0 = blockIdx.x * blockDim.x; p0 < head; p0 += stride) {
+        const int p = p0 + threadIdx.x;
+        bool cand = false;
+        int idx = -1;
+        if (p < head) {
+            const int ptr = __ldcg(&s.block_free[p]);
+            if (ptr >= 0 && ptr < s.nv) {
+                const short4 b = __ldcg(&s.block_pos[ptr]);
+                if (b.w) {
+                    idx = entry_of(s, b, ptr);
+                    cand = idx >= 0 && candidate<OUT>(s, w, __ldcg(reinterpret_cast<const int4 *>(s.entries) + idx), idx);
+                }
+            }
+        }
+        if (cand) {
+            const int q = warp_append(&w.hdr[5]);
+            if (q < w.k) w.sel[q] = idx;
+        }
+    }
+}
+
+// The ordered selection runs only when the scan found more than K.
+__device__ __forceinline__ bool scan_was_enough(const SwapDev &w)
+{
+    const int found = __ldcg(&w.hdr[5]);
+    if (found > w.k) return false;
+    if (blockIdx.x == 0 && threadIdx.x == 0) w.hdr[0] = found;
+    return true;
+}
+
 template <bool OUT>
 __global__ void __launch_bounds__(kSelThreads) swap_count_kernel(SceneDev s, SwapDev w)
 {
+    if (scan_was_enough(w)) return;  // uniform
     __shared__ int red[kSelThreads / 32];
     int c = 0;
     for (int r = 0; r < kRounds; ++r) {
@@ -195,6 +254,7 @@ __global__ void __launch_bounds__(kSelThreads) swap_count_kernel(SceneDev s, Swa
 template <bool OUT>
 __global__ void __launch_bounds__(kSelThreads) swap_select_kernel(SceneDev s, SwapDev w, int n_chunks)
 {
+    if (__ldcg(&w.hdr[5]) <= w.k) return;  // the scan's list is the selection
     __shared__ int red[kSelThreads / 32];
     int before = 0, all = 0;
     for (int c = threadIdx.x; c < n_chunks; c += kSelThreads) {
@@ -415,6 +475,11 @@ cudaError_t launch_select(const SceneDev &s, const SwapDev &w, cudaStream_t st)
     const int n_chunks = (s.nb + kChunk - 1) / kChunk;
     cudaError_t e = cudaMemsetAsync(w.hdr, 0, kHdrInts * sizeof(int32_t), st);
     if (e != cudaSuccess) return e;
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int g = std::max(1, std::min(4 * sms, (s.nv + 255) / 256));
+    swap_scan_kernel<OUT><<<g, 256, 0, st>>>(s, w);
     swap_count_kernel<OUT><<<n_chunks, kSelThreads, 0, st>>>(s, w);
     swap_select_kernel<OUT><<<n_chunks, kSelThreads, 0, st>>>(s, w, n_chunks);
     return cudaGetLastError();
