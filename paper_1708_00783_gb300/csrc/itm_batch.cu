@@ -196,7 +196,7 @@ __global__ void __launch_bounds__(256) batch_range_kernel(const ItemDev *__restr
     }
 }
 
-__global__ void __launch_bounds__(256) batch_raycast_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
+__global__ void __launch_bounds__(256, 4) batch_raycast_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
 {
     __shared__ int begin[kMaxItems + 1];
     const int n = head->n, total = head->cta_total;
