@@ -8,8 +8,8 @@ device volume, the host store and the per-entry swap states must agree bit
 for bit, compared by block coordinates (block indices and excess slots come
 from atomics).  Cases: the tiny sequence with a revisit and a tight bound
 (fusions deferred), a small hash table with long chains, learned (float)
-weights, a Kinect-scale run, a round trip against a run without swapping, and
-argument errors.
+weights, a Kinect-scale run, a round trip against a run without swapping, a
+reset, a block array too small even with swapping, and argument errors.
 """
 
 import numpy as np
@@ -188,3 +188,55 @@ def test_invalid_arguments(itm):
     assert g.swap_counters() == dict(host_data=0, swapped_out=0, waiting=0, moved_in=0, moved_out=0)
     c, F, W, S = g.swap_export_host()
     assert len(c) == 0
+
+
+def test_reset_clears_swapping_and_the_run_starts_over(itm):
+    """itm_scene_reset with swapping on: every entry back to "in device
+    memory" with nothing on the host, counters at 0; the same frames then
+    give what a fresh oracle gives."""
+    w = tiny_workload(n_frames=5)
+    g, o, _, _ = run(itm, w, list(range(5)), K=16, idle=1)
+    assert g.swap_counters()["swapped_out"] > 0
+    g.reset()
+    c = g.swap_counters()
+    assert c["host_data"] == 0 and c["waiting"] == 0 and c["moved_in"] == 0 and c["moved_out"] == 0
+    assert g.export()[0].shape[0] == 0 and len(g.swap_export_host()[0]) == 0
+    o2 = oracle.Scene(**w.params)
+    o2.swap_enable(16, 1)
+    ia = w.intr.as_array()
+    ci = itm.make_intrinsics(w.intr.width, w.intr.height, w.intr.fx, w.intr.fy, w.intr.cx, w.intr.cy)
+    for k in range(5):
+        f = w.frame(k)
+        D = dev(f.depth)
+        g.allocate(D, ci, f.T_wc)
+        g.swap_in()
+        g.integrate(D, ci, f.T_wc)
+        g.swap_out()
+        o2.allocate(f.depth, ia, f.T_wc)
+        o2.swap_in()
+        o2.integrate(f.depth, ia, f.T_wc)
+        o2.swap_out()
+    assert g.status() == 0
+    compare_volumes(g.export(), o2.export())
+    compare_host(g, o2)
+    compare_counters(g, o2)
+
+
+def test_block_array_too_small_even_with_swapping_is_reported(itm):
+    """A frame that meets more blocks than the device array holds fills it
+    whatever swapping moves out: the status says so (which blocks made it in
+    is then up to the order of the atomics, so only the status is compared)."""
+    w = tiny_workload(n_frames=2)
+    p = dict(w.params, num_blocks=256)
+    g, o = itm.Scene(**p), oracle.Scene(**p)
+    g.swap_enable(64, 1)
+    o.swap_enable(64, 1)
+    ci = itm.make_intrinsics(w.intr.width, w.intr.height, w.intr.fx, w.intr.fy, w.intr.cx, w.intr.cy)
+    f = w.frame(0)
+    g.allocate(dev(f.depth), ci, f.T_wc)
+    g.swap_in()
+    g.swap_out()
+    o.allocate(f.depth, w.intr.as_array(), f.T_wc)
+    assert itm.ERRORS.get(g.status()) == "ITM_ERR_VBA_FULL"
+    assert o.status & oracle.ST_VBA_FULL
+    assert g.stats()["allocated_blocks"] <= 256
