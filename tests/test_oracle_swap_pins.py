@@ -226,3 +226,23 @@ def test_bounded_swap_in_defers_the_fusion():
         assert not (cb & _keys(ch[st == oracle.Scene.SW_HOST]))
         assert cb | _keys(ch) == _keys(a.export()[0])
     assert waited > 0  # the bound was reached at least once
+
+
+def test_swapped_out_blocks_return_to_the_free_list():
+    """A full block array swapped out is free again: as many new keys fit,
+    and the swapped-out ones come back into the freed blocks too."""
+    p = scene_params(num_blocks=64)
+    sc = oracle.Scene(**p)
+    first = [(i, 0, 0) for i in range(64)]
+    for b in first:
+        sc.set_block(b, 0.5, 1.0)
+    assert sc.num_allocated == 64 and sc.status == 0
+    sc.swap_enable(1000, idle_frames=0)
+    assert sc.swap_out() == 64 and sc.num_allocated == 0
+    for i in range(64):
+        sc.set_block((i, 1, 0), 0.25, 2.0)
+    assert sc.num_allocated == 64 and sc.status == 0
+    assert sc.swap_out() == 64
+    for b in first:
+        sc.set_block(b, 0.75, 3.0)  # met again: fresh blocks, host data waiting
+    assert sc.num_allocated == 64 and sc.status == 0 and sc.swap_counters()["waiting"] == 64
