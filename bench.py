@@ -903,6 +903,12 @@ def run_ours(args, world, rank, local):
             "updated_voxels_per_frame": updated / args.steps,
         },
         "voxel_updates_per_s": updated_all / (total_ms_max / 1000.0),
+        "stage_rates": {
+            "allocation_pixels_per_s": n_pix * args.steps / (float(stage[:, 0].sum()) / 1000.0),
+            "integration_voxels_visited_per_s": visited / (integ_ms / 1000.0),
+            "integration_voxels_updated_per_s": updated / (integ_ms / 1000.0),
+            "raycast_rays_per_s": n_pix * args.steps / (float(stage[:, 2].sum()) / 1000.0),
+        },
         "roofline": {
             "kernel": "integrate_kernel<0>",
             "bound": "hbm",
