@@ -8,8 +8,8 @@ single-threaded, fp32 with every operation rounded separately, as the paper's
 listings are written in float); this module only marshals numpy arrays.
 
 Every function here is pinned by tests in ``tests/test_oracle_pins.py``,
-``tests/test_oracle_conf_pins.py``, ``tests/test_oracle_combined_pins.py``
-and ``tests/test_oracle_swap_pins.py``
+``tests/test_oracle_conf_pins.py``, ``tests/test_oracle_combined_pins.py``,
+``tests/test_oracle_swap_pins.py`` and ``tests/test_oracle_colour_pins.py``
 against closed forms, brute force and analytic geometry; see the docstrings
 there for which pin covers which step.
 """
@@ -117,6 +117,14 @@ def _load():
     lib.orc_swap_counters.argtypes = [P, i64p]
     lib.orc_swap_export_host.restype = I
     lib.orc_swap_export_host.argtypes = [P, P, P, P, P, I]
+    u8p = np.ctypeslib.ndpointer(np.uint8, flags="C_CONTIGUOUS")
+    lib.orc_colour_enable.restype = I
+    lib.orc_colour_enable.argtypes = [P]
+    lib.orc_integrate_colour.restype = ctypes.c_longlong
+    lib.orc_integrate_colour.argtypes = [P, f32p, I, I, f32p, f32p, u8p, I, I, f32p, f32p]
+    lib.orc_colour_at.argtypes = [P, f32p, ctypes.c_longlong, u8p]
+    lib.orc_export_colour.restype = I
+    lib.orc_export_colour.argtypes = [P, i16p, u8p, I]
     _lib = lib
     return lib
 
@@ -218,6 +226,42 @@ class Scene:
         out = np.zeros((max(n, 1), 3, 3), dtype=np.float32)
         _load().orc_mesh(self.p, out.ctypes.data, n)
         return out[:n]
+
+    # Sec. 3.1 colour voxels (readings in itm_oracle.c at colour_update)
+    def colour_enable(self):
+        if _load().orc_colour_enable(self.p) != 0:
+            raise ValueError("colour already on")
+
+    def integrate_colour(self, depth, intr, T_wc, rgb, intr_c, T_d2c=None) -> int:
+        """Depth integration plus the colour of rgb (uint8 [Hc, Wc, 3]) seen
+        by a camera with intrinsics intr_c (fx, fy, cx, cy) at T_d2c from the
+        depth camera (identity when None)."""
+        d = _f32(depth)
+        H, W = d.shape
+        rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
+        Hc, Wc = rgb.shape[:2]
+        T = np.eye(4, dtype=np.float32) if T_d2c is None else _f32(T_d2c)
+        n = _load().orc_integrate_colour(self.p, d, W, H, _f32(intr), _f32(T_wc).ravel(), rgb.ravel(), Wc, Hc,
+                                         _f32(intr_c), _f32(T).ravel())
+        if n < 0:
+            raise ValueError("colour is off")
+        return int(n)
+
+    def colour_at(self, pts):
+        """r, g, b, colour weight (uint8 [..., 4]) of the voxel nearest each
+        point (x, y, z, valid) of pts (float32 [..., 4])."""
+        p = _f32(pts)
+        out = np.zeros(p.shape[:-1] + (4,), dtype=np.uint8)
+        _load().orc_colour_at(self.p, p.reshape(-1), p.size // 4, out.reshape(-1))
+        return out
+
+    def export_colour(self):
+        """(coords int16 [n,3], rgbw uint8 [n,512,4]) in allocation order."""
+        n = self.num_allocated
+        coords = np.zeros((max(n, 1), 3), dtype=np.int16)
+        rgbw = np.zeros((max(n, 1), 512, 4), dtype=np.uint8)
+        _load().orc_export_colour(self.p, coords, rgbw.reshape(-1), n)
+        return coords[:n], rgbw[:n]
 
     # Sec. 5 swapping (readings in itm_oracle.c above orc_swap_enable)
     SW_HOST, SW_MERGE = 1, 2

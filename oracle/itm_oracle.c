@@ -27,6 +27,8 @@
  *                         the raycast maps, Gauss-Newton steps, pyramid
  *   orc_mesh              Sec. 4 Marching Cubes over the allocated blocks
  *   orc_depth_u16_to_f32  Sec. 4 (ViewBuilder: unsigned short -> float depth)
+ *   orc_integrate_colour  Sec. 3.1 colour voxel (RGB + colour weight) fused
+ *                         from an RGB frame beside the depth integration
  *   orc_swap_*            Sec. 5 swapping: a host block store with one slot
  *                         per hash entry, entries of swapped-out blocks kept
  *                         with ptr -1, at most K blocks moved per call, and
@@ -48,7 +50,8 @@
  *   - depth that is not > 0 (zero, negative or NaN) is no measurement;
  *   - learned weights: newW = w_px instead of 1, skipped when w_px <= 0;
  *   - raycast: see the comment above orc_raycast;
- *   - swapping: see the comment above orc_swap_enable.
+ *   - swapping: see the comment above orc_swap_enable;
+ *   - colour: see the comment above orc_colour_enable.
  */
 #include <math.h>
 #include <stdint.h>
@@ -93,6 +96,7 @@ typedef struct {
     int32_t *touch;       /* per entry: last allocation whose segments met the block */
     float **host;         /* per entry: the host slot (512 sdf then 512 weights), made on first use */
     long long swapped_in, swapped_out;
+    uint8_t *rgbw;        /* colour voxels (orc_colour_enable): nv * 512 * {r, g, b, colour weight} */
 } orc_scene;
 
 enum {
@@ -159,6 +163,7 @@ void orc_scene_free(orc_scene *s)
     free(s->host);
     free(s->swap_state);
     free(s->touch);
+    free(s->rgbw);
     free(s);
 }
 
@@ -186,6 +191,7 @@ static int take_block(orc_scene *s, int bx, int by, int bz)
         s->sdf[(size_t)ptr * ORC_BLOCK3 + i] = 1.0f; /* Sec. 3.1: float sdf starts at 1 */
         s->w[(size_t)ptr * ORC_BLOCK3 + i] = 0.0f;
     }
+    if (s->rgbw) memset(&s->rgbw[(size_t)ptr * ORC_BLOCK3 * 4], 0, ORC_BLOCK3 * 4); /* no colour observed */
     s->block_pos[3 * ptr + 0] = (int16_t)bx;
     s->block_pos[3 * ptr + 1] = (int16_t)by;
     s->block_pos[3 * ptr + 2] = (int16_t)bz;
@@ -373,12 +379,62 @@ int orc_allocate(orc_scene *s, const float *depth, int W, int H, const float int
 
 /* ------------------------------------------------------------- integration */
 
+static int coord_ok(float q);
+
+/* An RGB frame for the colour integration: 8-bit r, g, b per pixel
+ * (row-major, Wc x Hc), its intrinsics and the rigid map from depth-camera to
+ * colour-camera coordinates. */
+typedef struct {
+    const uint8_t *rgb;
+    int Wc, Hc;
+    float fx, fy, cx, cy;
+    float T[16];
+} colour_frame;
+
+/* Colour of voxel i of block ptr from the colour frame, the voxel at
+ * depth-camera coordinates (X, Y, Z).  Readings: the point maps into the
+ * colour camera by T (rows applied as row_apply), projects with the colour
+ * intrinsics and samples the image bilinearly (the 2x2 pixels at floor(u),
+ * floor(v) must be inside the image); each channel takes the running mean
+ * (w c + c_obs) / (w + 1) rounded half up to 8 bits, and the colour weight
+ * w grows by one up to max_w. */
+static void colour_update(orc_scene *s, int ptr, int i, float X, float Y, float Z, const colour_frame *cf)
+{
+    float Xc = row_apply(&cf->T[0], X, Y, Z);
+    float Yc = row_apply(&cf->T[4], X, Y, Z);
+    float Zc = row_apply(&cf->T[8], X, Y, Z);
+    if (!(Zc > 0.0f)) return;
+    float uc = (cf->fx * Xc) / Zc + cf->cx;
+    float vc = (cf->fy * Yc) / Zc + cf->cy;
+    if (!(uc >= 0.0f && vc >= 0.0f && uc < (float)(cf->Wc - 1) && vc < (float)(cf->Hc - 1))) return;
+    int u0 = (int)uc, v0 = (int)vc;
+    float a = uc - (float)u0, b = vc - (float)v0;
+    uint8_t *c = &s->rgbw[((size_t)ptr * ORC_BLOCK3 + i) * 4];
+    float wc = (float)c[3];
+    for (int ch = 0; ch < 3; ++ch) {
+        const uint8_t *P = cf->rgb;
+        float p00 = (float)P[((size_t)v0 * cf->Wc + u0) * 3 + ch];
+        float p10 = (float)P[((size_t)v0 * cf->Wc + u0 + 1) * 3 + ch];
+        float p01 = (float)P[((size_t)(v0 + 1) * cf->Wc + u0) * 3 + ch];
+        float p11 = (float)P[((size_t)(v0 + 1) * cf->Wc + u0 + 1) * 3 + ch];
+        float top = p00 + a * (p10 - p00);
+        float bot = p01 + a * (p11 - p01);
+        float obs = top + b * (bot - top);
+        float nc = (wc * (float)c[ch] + obs) / (wc + 1.0f);
+        int q = (int)(nc + 0.5f);
+        c[ch] = (uint8_t)(q < 0 ? 0 : (q > 255 ? 255 : q));
+    }
+    float nw = wc + 1.0f;
+    c[3] = (uint8_t)(nw < (float)s->max_w ? nw : (float)s->max_w);
+}
+
 /* Sec. 4.3: computeUpdatedVoxelDepthInfo applied to every voxel of every
  * allocated block.  wpx (nullable) holds a per-pixel observation weight that
- * replaces the constant 1 (learned-confidence mode).  Returns the number of
- * voxels updated. */
-long long orc_integrate(orc_scene *s, const float *depth, int W, int H, const float intr[4],
-                        const float T_wc[16], const float *wpx)
+ * replaces the constant 1 (learned-confidence mode); cf (nullable) an RGB
+ * frame whose colour is fused into the voxels that get a depth update within
+ * the band |eta| <= mu.  Returns the number of voxels updated. */
+static long long integrate_impl(orc_scene *s, const float *depth, int W, int H, const float intr[4],
+                                const float T_wc[16], const float *wpx, const colour_frame *cf)
 {
     float M[16];
     rigid_inverse(T_wc, M);
@@ -425,9 +481,71 @@ long long orc_integrate(orc_scene *s, const float *depth, int W, int H, const fl
                     F[i] = num / den;
                     Wt[i] = den < max_w ? den : max_w;
                     ++updated;
+                    if (cf && eta <= mu) colour_update(s, ptr, i, X, Y, Z, cf);
                 }
     }
     return updated;
+}
+
+long long orc_integrate(orc_scene *s, const float *depth, int W, int H, const float intr[4],
+                        const float T_wc[16], const float *wpx)
+{
+    return integrate_impl(s, depth, W, H, intr, T_wc, wpx, NULL);
+}
+
+/* Colour voxels (Sec. 3.1: the voxel types with colour carry an RGB value and
+ * a colour weight).  The paper gives the voxel, not its update; the readings
+ * are at colour_update.  Blocks start with colour 0 and colour weight 0. */
+int orc_colour_enable(orc_scene *s)
+{
+    if (s->rgbw) return -1;
+    s->rgbw = (uint8_t *)calloc((size_t)(s->nv > 0 ? s->nv : 1) * ORC_BLOCK3 * 4, 1);
+    return 0;
+}
+
+/* The depth integration of orc_integrate plus the colour of an RGB frame
+ * (rgb: Hc x Wc x 3 bytes; intr_c: fx, fy, cx, cy; T_d2c: depth-camera to
+ * colour-camera rigid map, row-major). */
+long long orc_integrate_colour(orc_scene *s, const float *depth, int W, int H, const float intr[4],
+                               const float T_wc[16], const uint8_t *rgb, int Wc, int Hc, const float intr_c[4],
+                               const float T_d2c[16])
+{
+    if (!s->rgbw) return -1;
+    colour_frame cf;
+    cf.rgb = rgb;
+    cf.Wc = Wc;
+    cf.Hc = Hc;
+    cf.fx = intr_c[0];
+    cf.fy = intr_c[1];
+    cf.cx = intr_c[2];
+    cf.cy = intr_c[3];
+    memcpy(cf.T, T_d2c, sizeof(cf.T));
+    return integrate_impl(s, depth, W, H, intr, T_wc, NULL, &cf);
+}
+
+/* Colour at n world points (x, y, z, valid; e.g. a raycast's vertex map):
+ * the colour voxel nearest to each valid point, r, g, b, colour weight; 0
+ * where the point is invalid or its voxel's block is not allocated.  Voxel
+ * coordinates q = p * (1/s) as in the raycast, nearest voxel floor(q + 1/2). */
+void orc_colour_at(const orc_scene *s, const float *pts, long long n, uint8_t *out)
+{
+    const float inv_s = (float)(1.0 / (double)s->voxel_size);
+    for (long long j = 0; j < n; ++j) {
+        uint8_t *o = &out[4 * j];
+        o[0] = o[1] = o[2] = o[3] = 0;
+        if (!s->rgbw || !(pts[4 * j + 3] > 0.0f)) continue;
+        int g[3];
+        int ok = 1;
+        for (int a = 0; a < 3; ++a) {
+            float q = pts[4 * j + a] * inv_s;
+            if (!coord_ok(q)) ok = 0;
+            else g[a] = (int)floorf(q + 0.5f);
+        }
+        if (!ok) continue;
+        int ptr = lookup(s, g[0] >> 3, g[1] >> 3, g[2] >> 3);
+        if (ptr < 0) continue;
+        memcpy(o, &s->rgbw[((size_t)ptr * ORC_BLOCK3 + (g[0] & 7) + 8 * (g[1] & 7) + 64 * (g[2] & 7)) * 4], 4);
+    }
 }
 
 /* ----------------------------------------------------------------- raycast */
@@ -1416,6 +1534,19 @@ int orc_export(const orc_scene *s, int16_t *coords, float *sdf, float *w, int ca
         memcpy(&coords[3 * k], &s->block_pos[3 * ptr], 3 * sizeof(int16_t));
         if (sdf) memcpy(&sdf[(size_t)k * ORC_BLOCK3], &s->sdf[(size_t)ptr * ORC_BLOCK3], ORC_BLOCK3 * sizeof(float));
         if (w) memcpy(&w[(size_t)k * ORC_BLOCK3], &s->w[(size_t)ptr * ORC_BLOCK3], ORC_BLOCK3 * sizeof(float));
+    }
+    return n;
+}
+
+/* Colour of the allocated blocks in allocation order: coords (3 x int16) and
+ * 512 x {r, g, b, colour weight}. */
+int orc_export_colour(const orc_scene *s, int16_t *coords, uint8_t *rgbw, int cap)
+{
+    int n = s->n_alloc < cap ? s->n_alloc : cap;
+    for (int k = 0; k < n && s->rgbw; ++k) {
+        int ptr = s->alloc_order[k];
+        memcpy(&coords[3 * k], &s->block_pos[3 * ptr], 3 * sizeof(int16_t));
+        memcpy(&rgbw[(size_t)k * ORC_BLOCK3 * 4], &s->rgbw[(size_t)ptr * ORC_BLOCK3 * 4], ORC_BLOCK3 * 4);
     }
     return n;
 }
