@@ -479,6 +479,47 @@ int itm_frame_blocks_noalloc(const float *depth_dev, const itm_intrinsics *intr,
                              int cap, int32_t *count_dev, itm_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Colour voxels (Sec. 3.1: the voxel types with colour carry an RGB value and
+ * a colour weight; the paper does not print their update).  A voxel that gets
+ * a depth update within the band -mu <= eta <= mu takes the colour of its
+ * projection into the RGB image: its depth-camera coordinates mapped by the
+ * depth-to-colour extrinsic, projected with the colour intrinsics, the image
+ * sampled bilinearly from the 2x2 pixels at the floor of the position (inside
+ * the image); each channel keeps the running mean (w c + c_obs) / (w + 1) in
+ * fp32 rounded half up to 8 bits, the colour weight counting observations up
+ * to max_w.  Constant observation weight (weight_mode 0) only; not with
+ * swapping or batches.
+ * ---------------------------------------------------------------------- */
+
+/* Allocates the colour voxels (num_blocks x 512 x 4 bytes: r, g, b, colour
+ * weight), all 0.  ITM_ERR_ARG when colour is already on, weight_mode is 1 or
+ * swapping is on; ITM_ERR_CUDA when the memory cannot be had.  Freed with the
+ * scene; itm_scene_reset clears it. */
+int itm_colour_enable(itm_scene *scene);
+
+/* itm_integrate plus the colour of an RGB frame: rgb_dev (device uint8
+ * [intr_colour.height][intr_colour.width][3], row-major r, g, b) seen by a
+ * camera with intrinsics intr_colour at T_d2c (host float[16], row-major
+ * rigid map from depth-camera to colour-camera coordinates).  Asynchronous;
+ * ITM_ERR_ARG when colour is off or an argument is invalid. */
+int itm_integrate_colour(itm_scene *scene, const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],
+                         const uint8_t *rgb_dev, const itm_intrinsics *intr_colour, const float T_d2c[16],
+                         itm_stream stream);
+
+/* Colour of the voxel nearest each of n world points (device float4[n]:
+ * x, y, z, valid > 0 -- e.g. a raycast's vertex map), written as r, g, b,
+ * colour weight to rgbw_dev (device uint8[n][4], 4-byte aligned); 0 where
+ * the point is invalid or its block is not allocated.  Voxel coordinates as
+ * in the raycast (p * (1/s)), nearest voxel floor(q + 1/2). */
+int itm_colour_at(itm_scene *scene, const float *points_dev, int64_t n, uint8_t *rgbw_dev, itm_stream stream);
+
+/* Colour of the allocated blocks, in the order of itm_scene_export: coords
+ * (host int16[cap][3]) and rgbw (host uint8[cap][512][4]); *n receives the
+ * number of blocks (cap 0 with null arrays asks for it).  Waits for the
+ * scene's last stream. */
+int itm_scene_export_colour(itm_scene *scene, int16_t *coords_host, uint8_t *rgbw_host, int cap, int *n);
+
+/* ------------------------------------------------------------------------
  * Sec. 5 swapping: only the active part of the map stays in device memory;
  * the rest lives in a host block store with one slot per hash entry (the
  * paper's objective O2: a hash entry index is the host address).  A

@@ -86,7 +86,7 @@ EXPORTED = [
     "itm_mlp_pack", "itm_conf_weights", "itm_conf_features", "itm_mlp_loss_grad", "itm_mlp_adam",
     "itm_batch_create", "itm_batch_destroy", "itm_batch_run", "itm_batch_set_tuning", "itm_batch_get_tuning",
     "itm_batch_set_graph", "itm_swap_enable", "itm_swap_in", "itm_swap_out", "itm_swap_get_counters",
-    "itm_swap_export_host",
+    "itm_swap_export_host", "itm_colour_enable", "itm_integrate_colour", "itm_colour_at", "itm_scene_export_colour",
 ]
 
 
@@ -142,6 +142,10 @@ def _load():
         "itm_swap_out": (I, [P, P]),
         "itm_swap_get_counters": (I, [P, ctypes.POINTER(itm_swap_counters)]),
         "itm_swap_export_host": (I, [P, P, P, P, P, I, ctypes.POINTER(I)]),
+        "itm_colour_enable": (I, [P]),
+        "itm_integrate_colour": (I, [P, P, ip, fp16, P, ip, fp16, P]),
+        "itm_colour_at": (I, [P, P, ctypes.c_int64, P, P]),
+        "itm_scene_export_colour": (I, [P, P, P, I, ctypes.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -466,6 +470,39 @@ def itm_batch_set_graph(batch, use_graph):
 
 # ------------------------------------------------------------ convenience
 
+# ------------------------------------------------------ Sec. 3.1 colour voxels
+
+def itm_colour_enable(scene):
+    _check(_lib.itm_colour_enable(scene), "itm_colour_enable")
+
+
+def itm_integrate_colour(scene, depth, intr, T_wc, rgb, intr_colour, T_d2c=None, stream=None):
+    """rgb: device uint8 tensor [Hc, Wc, 3]; intr_colour: itm_intrinsics of
+    the colour camera; T_d2c: depth-to-colour rigid map (identity if None)."""
+    a, p = _pose(T_wc)
+    b, q = _pose(np.eye(4, dtype=np.float32) if T_d2c is None else T_d2c)
+    _check(_lib.itm_integrate_colour(scene, _ptr(depth), ctypes.byref(intr), p, _ptr(rgb), ctypes.byref(intr_colour),
+                                     q, _stream(stream)), "itm_integrate_colour")
+
+
+def itm_colour_at(scene, points, out, stream=None):
+    """points: device float32 [..., 4]; out: device uint8 [..., 4]."""
+    n = points.numel() // 4
+    _check(_lib.itm_colour_at(scene, _ptr(points), int(n), _ptr(out), _stream(stream)), "itm_colour_at")
+
+
+def itm_scene_export_colour(scene):
+    """(coords int16 [n,3], rgbw uint8 [n,512,4]) in the order of itm_scene_export."""
+    n = ctypes.c_int(0)
+    _check(_lib.itm_scene_export_colour(scene, None, None, 0, ctypes.byref(n)), "itm_scene_export_colour")
+    cnt = n.value
+    coords = np.zeros((max(cnt, 1), 3), dtype=np.int16)
+    rgbw = np.zeros((max(cnt, 1), 512, 4), dtype=np.uint8)
+    _check(_lib.itm_scene_export_colour(scene, coords.ctypes.data, rgbw.ctypes.data, cnt, ctypes.byref(n)),
+           "itm_scene_export_colour")
+    return coords[:cnt], rgbw[:cnt]
+
+
 # ------------------------------------------------------------ Sec. 5 swapping
 
 SW_HOST, SW_MERGE = 1, 2
@@ -551,6 +588,18 @@ class Scene:
 
     def export(self, with_voxels=True):
         return itm_scene_export(self.handle, with_voxels)
+
+    def colour_enable(self):
+        itm_colour_enable(self.handle)
+
+    def integrate_colour(self, depth, intr, T_wc, rgb, intr_colour, T_d2c=None, stream=None):
+        itm_integrate_colour(self.handle, depth, intr, T_wc, rgb, intr_colour, T_d2c, stream)
+
+    def colour_at(self, points, out, stream=None):
+        itm_colour_at(self.handle, points, out, stream)
+
+    def export_colour(self):
+        return itm_scene_export_colour(self.handle)
 
     def swap_enable(self, transfer_blocks, idle_frames=1):
         itm_swap_enable(self.handle, transfer_blocks, idle_frames)

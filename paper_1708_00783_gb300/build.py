@@ -42,6 +42,7 @@ SOURCES = {
     "itm_batch.cu": ["-fmad=false"],
     "itm_combined.cu": ["-fmad=false"],
     "itm_swap.cu": ["-fmad=false"],
+    "itm_colour.cu": ["-fmad=false"],
     "itm_track.cu": ["-fmad=false"],
     "itm_mesh.cu": ["-fmad=false"],
 }

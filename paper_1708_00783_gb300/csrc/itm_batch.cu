@@ -374,7 +374,7 @@ int itm_batch_run(itm_batch *b, const itm_batch_item *items, int n, itm_stream s
         const itm_batch_item &x = items[i];
         if (!x.scene || !x.depth_dev || !valid_intr(&x.intr)) return ITM_ERR_ARG;
         if (x.scene->d.weight_mode != 0) return ITM_ERR_ARG;
-        if (x.scene->d.swap_state) return ITM_ERR_ARG;  // swapping scenes run through the per-scene calls
+        if (x.scene->d.swap_state || x.scene->d.rgbw) return ITM_ERR_ARG;  // swapping / colour: per-scene calls
         if (x.intr.width > kRangeMaxW || x.intr.height > kRangeMaxH) return ITM_ERR_ARG;
         if ((x.vertex_dev != nullptr) != (x.normal_dev != nullptr)) return ITM_ERR_ARG;
         if ((reinterpret_cast<uintptr_t>(x.vertex_dev) & 15) || (reinterpret_cast<uintptr_t>(x.normal_dev) & 15))

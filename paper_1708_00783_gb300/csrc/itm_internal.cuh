@@ -15,6 +15,7 @@
 //   swap_state  uint8[nb + ne]      Sec. 5 swapping (itm_swap_enable): kSw* per entry
 //   touch       int32[nv]           last allocation whose segments met the block (-1: freed
 //                                   by the running swap-out)
+//   rgbw        uint32[nv][512]     colour voxels (itm_colour_enable): bytes r, g, b, colour weight
 //   host store  pinned host memory mapped into the device, one slot per entry:
 //               float[nb + ne][512] sdf and uint8 / float [nb + ne][512] weights
 #pragma once
@@ -101,6 +102,7 @@ struct SceneDev {
     uint8_t *swap_state;
     int32_t *touch;
     int swap_frame;  // allocations since swapping was enabled
+    uint32_t *rgbw;  // colour voxels (Sec. 3.1): null while colour is off
     int nb, ne, nv;
     int ovf_cap;
     float voxel_size, mu, z_min, z_max;

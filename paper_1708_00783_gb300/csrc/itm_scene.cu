@@ -190,6 +190,7 @@ int itm_scene_destroy(itm_scene *sc)
     if (!sc) return ITM_ERR_ARG;
     cudaDeviceSynchronize();
     swap_free(sc);
+    if (sc->d.rgbw) cudaFree(sc->d.rgbw);
     free_dev(sc->d);
     free(sc);
     return ITM_OK;
@@ -204,6 +205,8 @@ int itm_scene_reset(itm_scene *sc, itm_stream stream)
     sc->last_stream = st;
     cudaError_t e = launch_reset(sc->d, st);
     if (e == cudaSuccess) e = swap_reset(sc, st);
+    if (e == cudaSuccess && sc->d.rgbw)
+        e = cudaMemsetAsync(sc->d.rgbw, 0, sizeof(uint32_t) * (size_t)(sc->d.nv > 0 ? sc->d.nv : 1) * kBlockVoxels, st);
     return check_cuda(e);
 }
 
@@ -678,6 +681,8 @@ int itm_scene_import(itm_scene *sc, const int16_t *coords_host, const float *sdf
     cudaError_t e = cudaStreamSynchronize(sc->last_stream);
     if (e == cudaSuccess) e = launch_reset(d, 0);
     if (e == cudaSuccess) e = swap_reset(sc, 0);
+    if (e == cudaSuccess && d.rgbw)
+        e = cudaMemsetAsync(d.rgbw, 0, sizeof(uint32_t) * (size_t)(d.nv > 0 ? d.nv : 1) * kBlockVoxels, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e == cudaSuccess)
         e = cudaMemcpy(d.entries, E.data(), sizeof(Entry) * E.size(), cudaMemcpyHostToDevice);

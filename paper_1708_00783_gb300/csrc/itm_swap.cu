@@ -497,6 +497,7 @@ int itm_swap_enable(itm_scene *sc, int transfer_blocks, int idle_frames)
 {
     if (!sc || transfer_blocks < 1 || transfer_blocks > (1 << 24) || idle_frames < 0) return ITM_ERR_ARG;
     if (sc->d.swap_state) return ITM_ERR_ARG;  // already on
+    if (sc->d.rgbw) return ITM_ERR_ARG;        // colour voxels are not swapped
     SceneDev &d = sc->d;
     const size_t slots = (size_t)d.nb + (size_t)d.ne;
     const size_t wbytes = d.weight_mode == 0 ? 1 : 4;
