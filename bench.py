@@ -288,13 +288,14 @@ def run_reference(args, world, rank):
     """Reference arm: the CPU oracle timed on this arm's workload and metric."""
     if rank != 0:
         return
-    frames = render_frames(0, list(range(0, N_FRAMES, 30)))
+    n_frames, workload_desc, metric = WORKLOADS[args.workload]
+    stride = max(1, n_frames // 10)
+    order = list(range(0, n_frames, stride))
+    frames = render_frames(0, order, name=args.workload)
     import oracle
-    from synth import kinect_workload
-    w = kinect_workload()
+    w = make_workload(args.workload, 0)
     sc = oracle.Scene(**w.params)
     ia = w.intr.as_array()
-    order = list(range(0, N_FRAMES, 30))
     budget = 120.0
     for i in range(min(args.warmup, 2)):
         raw, T = frames[order[i % len(order)]]
@@ -317,14 +318,18 @@ def run_reference(args, world, rank):
     total = sum(times)
     val = len(times) / total
     line = {
-        "impl": "reference", "metric": METRIC, "value": val, "unit": "frames/s", "n_gpus": world,
+        "impl": "reference", "metric": metric, "value": val, "unit": "frames/s", "n_gpus": world,
         "steps": len(times), "warmup": min(args.warmup, 2), "ms_per_step": 1000 * total / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD_NAME, "frames": "every 30th frame of the trajectory, repeated",
+        "config": {"workload": workload_desc,
+                   "frames": ("every frame of the trajectory, repeated" if stride == 1 else
+                              "every %d-th frame of the trajectory, repeated" % stride),
                    "requested_steps": args.steps, "time_budget_s": budget},
         "cpu_baseline": {"value": val, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                         "sample": "%d steps of one full 640x480 frame each (frames 0,30,...,270 cycled), "
-                                   "single-threaded C oracle, stopped after a %.0f s budget" % (len(times), budget)},
+                         "sample": "%d steps of one full %dx%d frame each (frames %s cycled), single-threaded C "
+                                   "oracle, stopped after a %.0f s budget"
+                                   % (len(times), w.intr.width, w.intr.height,
+                                      ",".join(str(k) for k in order[:3]) + ",...," + str(order[-1]), budget)},
         "e2e": {"value": val, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "voxel_updates_per_s": upd / total,
     }
