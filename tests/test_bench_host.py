@@ -1,0 +1,38 @@
+"""bench.py's host-side helpers (CPU): the committed traffic is reported only
+while the integration source matches the captured one, the roofline peak
+comes from the measured file (else the stated fallback), and throughput is
+the whole job's units over the slowest rank's time."""
+
+import json
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_committed_traffic_follows_the_integration_source(monkeypatch):
+    with open(os.path.join(ROOT, "profiles", "integrate_kinect_traffic.json")) as f:
+        d = json.load(f)
+    if d["integrate_source_sha256_16"] == bench.integrate_source_hash():
+        assert bench.committed_traffic() == d["dram_bytes_per_launch_mean"] > 0
+    else:  # the kernel changed since the capture: no traffic is reported
+        assert bench.committed_traffic() is None
+    monkeypatch.setattr(bench, "integrate_source_hash", lambda: d["integrate_source_sha256_16"])
+    assert bench.committed_traffic() == d["dram_bytes_per_launch_mean"]
+    monkeypatch.setattr(bench, "integrate_source_hash", lambda: "0" * 16)
+    assert bench.committed_traffic() is None
+
+
+def test_peak_from_the_measured_file_else_the_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.load_peaks() == (6800.0, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6781.4, "bf16_tflops": 1900.0}))
+    assert bench.load_peaks() == (6781.4, "measured")
+
+
+def test_job_throughput_counts_all_ranks_over_the_slowest():
+    assert bench.job_throughput(290, 1, 58.0) == 290 / 0.058
+    assert bench.job_throughput(290, 4, 60.0) == 4 * 290 / 0.060
