@@ -51,7 +51,7 @@ enum {
     ITM_ERR_OVERFLOW = 7,  /* status: a per-frame work list overflowed */
     ITM_ERR_TOO_LARGE = 8, /* the input could exceed a fixed-size buffer of the call */
     ITM_ERR_SINGULAR = 9,  /* a tracking step has no unique solution (fewer than 6 constrained motions) */
-    ITM_ERR_BOUNDS = 10,   /* status: an index check failed (bounds-checked builds, ITM_CHECK_BOUNDS) */
+    ITM_ERR_BOUNDS = 10,   /* status: an index check failed (bounds-checked builds; the swap kernels always) */
 };
 
 /* Sticky status bits (itm_stats.status). */
@@ -60,7 +60,8 @@ enum {
 #define ITM_ST_RANGE 0x4u
 #define ITM_ST_TIMEOUT 0x8u
 #define ITM_ST_OVERFLOW 0x10u
-#define ITM_ST_BOUNDS 0x20u /* only in builds with -DITM_CHECK_BOUNDS: an index was out of range, the access skipped */
+#define ITM_ST_BOUNDS 0x20u /* an index was out of range, the access skipped: in builds with -DITM_CHECK_BOUNDS,
+                              * and in every build for a swap entry that is not what its selection said */
 
 /* Pinhole depth intrinsics (Sec. 6 calibration file: image size, focal
  * length and principal point in pixels; Sec. 4.3 projParams_d). */
