@@ -57,3 +57,17 @@ def test_host_hash_index_follows_printed_function():
 def test_version_string():
     import paper_1708_00783_gb300 as itm
     assert "sm_103a" in itm.itm_version()
+
+
+def test_binding_knows_every_error_code_and_constant():
+    """Every ITM_ERR_* value of the header has its name in the binding's error
+    map, and the binding's copies of the header's #define constants agree."""
+    import paper_1708_00783_gb300 as itm
+    text = open(os.path.join(ROOT, "include", "itm.h")).read()
+    codes = {int(v): n for n, v in re.findall(r"(ITM_ERR_[A-Z_]+)\s*=\s*(\d+)", text)}
+    assert codes and codes == itm.ERRORS
+    defines = dict(re.findall(r"#define\s+(ITM_[A-Z0-9_]+)\s+\(?([0-9]+)", text))
+    for name in ("ITM_MLP_FEATURES", "ITM_MLP_HIDDEN", "ITM_MLP_PARAMS", "ITM_MLP_PACKED_BYTES",
+                 "ITM_MLP_SCRATCH_PER_SAMPLE", "ITM_BATCH_STAGES"):
+        if name in defines and hasattr(itm, name):
+            assert int(defines[name]) == getattr(itm, name), name
