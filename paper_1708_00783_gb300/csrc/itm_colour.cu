@@ -24,18 +24,11 @@
 #include <algorithm>
 #include <vector>
 
-#include <nvtx3/nvToolsExt.h>
-
 #include "itm_ops.cuh"
 
 namespace itm {
 
 namespace {
-
-struct Range {
-    explicit Range(const char *name) { nvtxRangePushA(name); }
-    ~Range() { nvtxRangePop(); }
-};
 
 struct ColourFrame {
     const uint8_t *rgb;  // Hc x Wc x 3 bytes, row-major

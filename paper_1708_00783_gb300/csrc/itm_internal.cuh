@@ -21,6 +21,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include "itm.h"
@@ -248,6 +249,13 @@ struct itm_scene {
     void *host_sdf, *host_w;
     void *swap_scratch;
     int swap_k, swap_idle;
+};
+
+// An NVTX range named after a C-ABI call for the duration of the call, so
+// profiler timelines group each call's kernels (no cost without a profiler).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
 };
 
 // Host helpers implemented in itm_scene.cu.

@@ -10,17 +10,6 @@
 
 #include "itm_internal.cuh"
 
-#include <nvtx3/nvToolsExt.h>
-
-namespace {
-// An NVTX range named after the C-ABI call for the duration of the call, so
-// profiler timelines group each call's kernels (no cost without a profiler).
-struct Range {
-    explicit Range(const char *name) { nvtxRangePushA(name); }
-    ~Range() { nvtxRangePop(); }
-};
-}  // namespace
-
 namespace itm {
 
 int overflow_capacity();  // itm_alloc.cu

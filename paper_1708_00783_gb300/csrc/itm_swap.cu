@@ -38,19 +38,11 @@
 #include <algorithm>
 #include <vector>
 
-#include <nvtx3/nvToolsExt.h>
-
 #include "itm_ops.cuh"
 
 namespace itm {
 
 namespace {
-
-// NVTX range named after the C-ABI call
-struct Range {
-    explicit Range(const char *name) { nvtxRangePushA(name); }
-    ~Range() { nvtxRangePop(); }
-};
 
 constexpr int kSelThreads = 256;
 constexpr int kRounds = 4;
