@@ -1,0 +1,130 @@
+"""Planted mistakes in a copy of the oracle fail its pins (CPU).
+
+Each case copies oracle/ with one source line changed, plus tests/ and synth/,
+into a temporary directory and runs there the pin module for that part of the
+oracle; the module must fail, on an assertion (not on a build error).  This is
+what ties the pins to something other than the oracle itself: a plausible
+slip in an operation, an index, an order, a sign or a bound breaks at least
+one of them.  The mistakes are planted in the oracle only, on the CPU.
+"""
+
+import os
+import shutil
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CORE = "test_oracle_pins.py"
+CONF = "test_oracle_conf_pins.py"
+SWAP = "test_oracle_swap_pins.py"
+COLOUR = "test_oracle_colour_pins.py"
+
+# (pin module, mistake, original text, planted text)
+MUTANTS = [
+    # allocation, integration, raycast (Sec. 3-4)
+    (CORE, "voxel centre instead of corner", "                    float px = (float)(bx * 8 + lx) * vs;",
+     "                    float px = ((float)(bx * 8 + lx) + 0.5f) * vs;"),
+    (CORE, "no truncation of f", "                    if (f > 1.0f) f = 1.0f;", ""),
+    (CORE, "sign of eta", "                    float eta = d - Z;", "                    float eta = Z - d;"),
+    (CORE, "pose inverse not transposed", "        for (int j = 0; j < 3; ++j) M[4 * i + j] = (float)R[j][i];",
+     "        for (int j = 0; j < 3; ++j) M[4 * i + j] = (float)R[i][j];"),
+    (CORE, "DDA drops the last block", "    while (left[0] + left[1] + left[2] > 0) {",
+     "    while (left[0] + left[1] + left[2] > 1) {"),
+    (CORE, "wrong excess index", "        if (e->offset < 1) return -1;\n        idx = s->nb + e->offset - 1;",
+     "        if (e->offset < 1) return -1;\n        idx = s->nb + e->offset;"),
+    (CORE, "wrong hash prime", "    uint32_t hx = (uint32_t)x * 73856093u;", "    uint32_t hx = (uint32_t)x * 73856092u;"),
+    (CORE, "pixel index without rounding", "                    int pix = (int)(u + 0.5f) + (int)(v + 0.5f) * W;",
+     "                    int pix = (int)(u) + (int)(v) * W;"),
+    (CORE, "depth by a reciprocal multiply", "    for (long long i = 0; i < n; ++i) out[i] = (float)raw[i] / 1000.0f;",
+     "    for (long long i = 0; i < n; ++i) out[i] = (float)raw[i] * 0.001f;"),
+    (CORE, "refinement step sign", "                t = t + F * tmu;\n            }\n            float p[3];",
+     "                t = t - F * tmu;\n            }\n            float p[3];"),
+    (CORE, "normal sign", "                float fm = trilinear(s, qm, &obs);\n                g[a] = fp - fm;",
+     "                float fm = trilinear(s, qm, &obs);\n                g[a] = fm - fp;"),
+    # learned confidence weight
+    (CONF, "bf16 by truncation", "    u += 0x7fffu + lsb;\n    u &= 0xffff0000u;", "    u &= 0xffff0000u;"),
+    (CONF, "bf16 ties away from zero", "    u += 0x7fffu + lsb;", "    u += 0x8000u; (void)lsb;"),
+    (CONF, "feature clamp at 3", "                if (f > 4.0) f = 4.0;\n                if (f < -4.0) f = -4.0;",
+     "                if (f > 3.0) f = 3.0;\n                if (f < -3.0) f = -3.0;"),
+    (CONF, "patch index transposed", "            x[(i + 3) * 7 + (j + 3)] = f;", "            x[(j + 3) * 7 + (i + 3)] = f;"),
+    (CONF, "feature sign", "                f = (d - dc) / (double)mu;", "                f = (dc - d) / (double)mu;"),
+    (CONF, "normal cross product order",
+     "        double n[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};",
+     "        double n[3] = {b[1] * a[2] - b[2] * a[1], b[2] * a[0] - b[0] * a[2], b[0] * a[1] - b[1] * a[0]};"),
+    (CONF, "no ReLU on layer 2", "        a2[n] = relu(acc + b2[n]);", "        a2[n] = acc + b2[n];"),
+    (CONF, "b2 dropped", "        a2[n] = relu(acc + b2[n]);", "        a2[n] = relu(acc);"),
+    (CONF, "b3 dropped", "    double o = b3[0];", "    double o = 0.0; (void)b3;"),
+    (CONF, "gradient not averaged", "        double dout = (p - t) / n;", "        double dout = (p - t);"),
+    (CONF, "layer-2 gradient not masked", "            d2[k] = h2[k] > 0.0 ? dout * w3[k] : 0.0;",
+     "            d2[k] = dout * w3[k];"),
+    (CONF, "layer-1 gradient not masked", "            d1[m] = h1[m] > 0.0 ? acc : 0.0;", "            d1[m] = acc;"),
+    (CONF, "W2 gradient transposed",
+     "            for (int m = 0; m < ORC_NH; ++m) gW2[a * ORC_NH + m] += d2[a] * maybe_bf16(h1[m], round_bf16);",
+     "            for (int m = 0; m < ORC_NH; ++m) gW2[m * ORC_NH + a] += d2[a] * maybe_bf16(h1[m], round_bf16);"),
+    (CONF, "sign of the label term", "        loss += (o > 0 ? o : 0.0) - o * t + log1p(exp(-fabs(o)));",
+     "        loss += (o > 0 ? o : 0.0) + o * t + log1p(exp(-fabs(o)));"),
+    # swapping (Sec. 5)
+    (SWAP, "no weight clamp", "    *W = den < max_w ? den : max_w;", "    *W = den;"),
+    (SWAP, "host weight 0 not skipped", "    if (!(Wh > 0.0f)) return;\n    if (!(*W > 0.0f)) {",
+     "    if (!(*W > 0.0f) && (Wh > 0.0f)) {"),
+    (SWAP, "device weight 0 not taken over", "    if (!(*W > 0.0f)) {\n        *F = Fh;", "    if (0) {\n        *F = Fh;"),
+    (SWAP, "descending key in a chain",
+     "packed_key(&s->entries[chain[j - 1]]) > packed_key(&s->entries[idx])",
+     "packed_key(&s->entries[chain[j - 1]]) < packed_key(&s->entries[idx])"),
+    (SWAP, "buckets in reverse order",
+     "for (int h = 0; h < s->nb && n < cap; ++h) {\n        if (s->entries[h].ptr < -1) continue;",
+     "for (int hh = 0; hh < s->nb && n < cap; ++hh) {\n        const int h = s->nb - 1 - hh;\n"
+     "        if (s->entries[h].ptr < -1) continue;"),
+    (SWAP, "freed block not returned",
+     "        s->block_free[s->block_top++] = ptr;\n    }\n    free(sel);\n    s->swapped_out += n;",
+     "    }\n    free(sel);\n    s->swapped_out += n;"),
+    (SWAP, "swapped-out key inserted again", "        if (e->x == bx && e->y == by && e->z == bz) { /* present */",
+     "        if (e->x == bx && e->y == by && e->z == bz && e->ptr != -1) { /* present */"),
+    (SWAP, "blocks met again not stamped", "            touch_entry(s, e);\n            return;\n        }",
+     "            return;\n        }"),
+    (SWAP, "allocation count not advanced", "    if (s->swap_on) ++s->frame;", ""),
+    (SWAP, "fused entry left waiting",
+     "        s->swap_state[idx] = ORC_SW_DEVICE;\n    }\n    free(sel);\n    s->swapped_in += n;",
+     "    }\n    free(sel);\n    s->swapped_in += n;"),
+    (SWAP, "swap-in ignores the bound", "    const int n = select_entries(s, wants_in, sel, s->swap_k);",
+     "    free(sel);\n    sel = (int32_t *)malloc(sizeof(int32_t) * (size_t)(s->nb + s->ne));\n"
+     "    const int n = select_entries(s, wants_in, sel, s->nb + s->ne);"),
+    (SWAP, "idle test off by one", "s->frame - s->touch[idx] >= s->swap_idle", "s->frame - s->touch[idx] > s->swap_idle"),
+    # colour voxels (Sec. 3.1)
+    (COLOUR, "colour outside the band", "                    if (cf && eta <= mu) colour_update",
+     "                    if (cf) colour_update"),
+    (COLOUR, "band of 2 mu", "                    if (cf && eta <= mu) colour_update",
+     "                    if (cf && eta <= 2.0f * mu) colour_update"),
+    (COLOUR, "rounding by truncation", "        int q = (int)(nc + 0.5f);", "        int q = (int)(nc);"),
+    (COLOUR, "colour weight not capped", "    c[3] = (uint8_t)(nw < (float)s->max_w ? nw : (float)s->max_w);",
+     "    c[3] = (uint8_t)nw;"),
+    (COLOUR, "bilinear axes swapped", "    float a = uc - (float)u0, b = vc - (float)v0;",
+     "    float b = uc - (float)u0, a = vc - (float)v0;"),
+    (COLOUR, "extrinsic ignored", "    float Xc = row_apply(&cf->T[0], X, Y, Z);", "    float Xc = X; (void)row_apply;"),
+    (COLOUR, "channels reversed", "        float p00 = (float)P[((size_t)v0 * cf->Wc + u0) * 3 + ch];",
+     "        float p00 = (float)P[((size_t)v0 * cf->Wc + u0) * 3 + (2 - ch)];"),
+    (COLOUR, "colour weight steps by 2", "    float nw = wc + 1.0f;", "    float nw = wc + 2.0f;"),
+    (COLOUR, "point colour from floor(q)", "            else g[a] = (int)floorf(q + 0.5f);",
+     "            else g[a] = (int)floorf(q);"),
+]
+
+
+@pytest.mark.parametrize("module,mistake,old,new", MUTANTS, ids=[m[1] for m in MUTANTS])
+def test_planted_mistake_fails_a_pin(tmp_path, module, mistake, old, new):
+    src = open(os.path.join(ROOT, "oracle", "itm_oracle.c")).read()
+    assert src.count(old) == 1, "the planted line no longer matches the oracle once: " + mistake
+    for d in ("tests", "synth"):
+        shutil.copytree(os.path.join(ROOT, d), tmp_path / d, ignore=shutil.ignore_patterns("__pycache__"))
+    (tmp_path / "oracle").mkdir()
+    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), tmp_path / "oracle" / "__init__.py")
+    (tmp_path / "oracle" / "itm_oracle.c").write_text(src.replace(old, new))
+    # the pin modules need no GPU check (and so no torch import) in the copy
+    (tmp_path / "tests" / "conftest.py").write_text(
+        "import os, sys\nsys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))\n")
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "tests/" + module],
+                       cwd=tmp_path, capture_output=True, text=True, timeout=900)
+    assert r.returncode != 0, "the pins did not catch: " + mistake
+    assert "assert" in r.stdout, "failed for another reason than an assertion:\n" + r.stdout[-2000:]
