@@ -21,6 +21,9 @@ CORE = "test_oracle_pins.py"
 CONF = "test_oracle_conf_pins.py"
 SWAP = "test_oracle_swap_pins.py"
 COLOUR = "test_oracle_colour_pins.py"
+COMB = "test_oracle_combined_pins.py"
+TRACK = "test_oracle_track_pins.py"
+MESH = "test_oracle_mesh_pins.py"
 
 # (pin module, mistake, original text, planted text)
 MUTANTS = [
@@ -108,7 +111,52 @@ MUTANTS = [
      "        float p00 = (float)P[((size_t)v0 * cf->Wc + u0) * 3 + (2 - ch)];"),
     (COLOUR, "colour weight steps by 2", "    float nw = wc + 1.0f;", "    float nw = wc + 2.0f;"),
     (COLOUR, "point colour from floor(q)", "            else g[a] = (int)floorf(q + 0.5f);",
-     "            else g[a] = (int)floorf(q);"),
+     "            else g[a] = (int)floorf(q);"),    # combined map (Sec. 7.2), depth tracker (Sec. 4.1.1), Marching Cubes (Sec. 4)
+    (COMB, "combined sum not normalised", "    return dsum > 0.0f ? num / dsum : 1.0f;", "    return dsum > 0.0f ? num : 1.0f;"),
+    (COMB, "sign of a combined term", "        num = num + Wt * F;", "        num = num - Wt * F;"),
+    (COMB, "weight taken at one corner", "    *Wt = out[1];", "    *Wt = w[0];"),
+    (COMB, "submap pose transposed", "        q[r] = row_apply(P + 4 * r, X[0], X[1], X[2]) * inv_s;",
+     "        q[r] = (((P[r] * X[0] + P[4 + r] * X[1]) + P[8 + r] * X[2]) + P[4 * r + 3]) * inv_s;"),
+    (COMB, "first submap only",
+     "    for (int i = 0; i < n; ++i) {\n        float q[3];\n        if (!submap_coords(P + 16 * i, X, inv_s, q)) continue;\n        float F, Wt;",
+     "    for (int i = 0; i < 1 && i < n; ++i) {\n        float q[3];\n        if (!submap_coords(P + 16 * i, X, inv_s, q)) continue;\n        float F, Wt;"),
+    (COMB, "allocation test on the first submap only",
+     "    for (int i = 0; i < n; ++i) {\n        float q[3];\n        if (!submap_coords(P + 16 * i, X, inv_s, q)) continue;\n        int bx",
+     "    for (int i = 0; i < 1 && i < n; ++i) {\n        float q[3];\n        if (!submap_coords(P + 16 * i, X, inv_s, q)) continue;\n        int bx"),
+    (COMB, "default 0 where unobserved", "    return dsum > 0.0f ? num / dsum : 1.0f;", "    return dsum > 0.0f ? num / dsum : 0.0f;"),
+    (TRACK, "cross product order in the Jacobian",
+     "            const float J[6] = {pw[1] * Np[2] - pw[2] * Np[1], pw[2] * Np[0] - pw[0] * Np[2],\n"
+     "                                pw[0] * Np[1] - pw[1] * Np[0], Np[0], Np[1], Np[2]};",
+     "            const float J[6] = {Np[1] * pw[2] - Np[2] * pw[1], Np[2] * pw[0] - Np[0] * pw[2],\n"
+     "                                Np[0] * pw[1] - Np[1] * pw[0], Np[0], Np[1], Np[2]};"),
+    (TRACK, "update multiplied on the right", "            for (int m = 0; m < 3; ++m) acc += R[i][m] * (double)T[4 * m + j];",
+     "            for (int m = 0; m < 3; ++m) acc += (double)T[4 * i + m] * R[m][j];"),
+    (TRACK, "association without rounding",
+     "            const size_t o = 4 * ((size_t)(int)(vr + 0.5f) * Wr + (int)(ur + 0.5f));",
+     "            const size_t o = 4 * ((size_t)(int)(vr) * Wr + (int)(ur));"),
+    (TRACK, "invalid depths in the pyramid mean", "                if (d > 0.0f) {\n                    sum = sum + d;",
+     "                if (1) {\n                    sum = sum + d;"),
+    (TRACK, "pyramid centre c/2", "    out[2] = (in[2] - 0.5f) / 2.0f;", "    out[2] = in[2] / 2.0f;"),
+    (TRACK, "residual sign", "            const float res = (dx * Np[0] + dy * Np[1]) + dz * Np[2];",
+     "            const float res = -((dx * Np[0] + dy * Np[1]) + dz * Np[2]);"),
+    (TRACK, "threshold on the distance, not its square", "            if (!(dist2 <= t2)) continue;",
+     "            if (!(dist2 <= dist_thresh)) continue;"),
+    (TRACK, "Rodrigues sine sign",
+     "R[i][j] = (i == j ? 1.0 : 0.0) + a * K[i][j] + c * K2[i][j];",
+     "R[i][j] = (i == j ? 1.0 : 0.0) - a * K[i][j] + c * K2[i][j];"),
+    (MESH, "ambiguous faces joined around outside corners", "                int want = (posA[k] + 3) & 3;",
+     "                int want = (posA[k] + 1) & 3;"),
+    (MESH, "fan not flipped", "            tri[3 * n_tri + 1] = loop[i + 1];\n            tri[3 * n_tri + 2] = loop[i];",
+     "            tri[3 * n_tri + 1] = loop[i];\n            tri[3 * n_tri + 2] = loop[i + 1];"),
+    (MESH, "crossing t from the wrong end", "                    float tt = F[a] / (F[a] - F[c]);",
+     "                    float tt = F[c] / (F[c] - F[a]);"),
+    (MESH, "weights not checked", "    if (!(s->w[i] > 0.0f)) return 0;\n    *F = s->sdf[i];", "    *F = s->sdf[i];"),
+    (MESH, "edge numbering swapped", "    return 4 * axis + o1 + 2 * o2;", "    return 4 * axis + 2 * o1 + o2;"),
+    (MESH, "a face walked clockwise", "    {0, 4, 6, 2}, {1, 3, 7, 5},", "    {0, 2, 6, 4}, {1, 3, 7, 5},"),
+    (MESH, "F = 0 taken as inside", "            int ia = F[a] < 0.0f, ib = F[b] < 0.0f;",
+     "            int ia = F[a] <= 0.0f, ib = F[b] <= 0.0f;"),
+    (MESH, "corner offset on the wrong axis", "                        float coord = (float)(g[k] + ((a >> k) & 1));",
+     "                        float coord = (float)(g[k] + ((a >> ((k + 1) % 3)) & 1));"),
 ]
 
 
