@@ -257,13 +257,31 @@ def sum_over_ranks(value, world, device=None):
 
 # ----------------------------------------------------------------- CPU oracle
 
-def cpu_oracle_sample(frames, stride=30, budget_s=30.0, name="kinect"):
-    """The oracle as it stands, single-threaded, on every `stride`-th frame of
-    the trajectory from an empty volume (alloc + integrate + raycast each),
-    stopping once `budget_s` of work is done."""
+def host_cpu():
+    """CPU model and logical core count of this host, for the CPU baseline."""
+    import platform
+    model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return "%s (%s), %d logical cores" % (model or platform.processor() or "unknown CPU", platform.machine(),
+                                          os.cpu_count() or 0)
+
+
+def cpu_oracle_sample(frames, stride=30, budget_s=30.0, name="kinect", threaded=False):
+    """The oracle as it stands on every `stride`-th frame of the trajectory
+    from an empty volume (alloc + integrate + raycast each), stopping once
+    `budget_s` of work is done: single-threaded, or (threaded) the same source
+    built with OpenMP on all host cores, whose results are identical."""
     import oracle
     w = make_workload(name, 0)
-    sc = oracle.Scene(**w.params)
+    sc = oracle.Scene(**w.params, threaded=threaded)
+    cores = oracle.threads() if threaded else 1
     ia = w.intr.as_array()
     done, t0, upd = 0, time.perf_counter(), 0
     idx = sorted(frames)
@@ -277,11 +295,12 @@ def cpu_oracle_sample(frames, stride=30, budget_s=30.0, name="kinect"):
         if time.perf_counter() - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
-    return {"value": done / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+    return {"value": done / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
             "sample": "%d frames (every %dth of the %d-frame trajectory from frame 0, empty volume at start), "
-                      "u16->f32 + allocate + integrate over all allocated blocks + raycast, single thread"
-                      % (done, stride, WORKLOADS[name][0]),
-            "voxel_updates_per_s": upd / dt, "seconds": dt}
+                      "u16->f32 + allocate + integrate over all allocated blocks + raycast, %s"
+                      % (done, stride, WORKLOADS[name][0],
+                         "OpenMP build, %d threads" % cores if threaded else "single thread"),
+            "voxel_updates_per_s": upd / dt, "seconds": dt, "host": host_cpu()}
 
 
 def run_reference(args, world, rank):
@@ -927,10 +946,16 @@ def run_ours(args, world, rank, local):
     if extra and args.learned:
         learned_rep = run_learned_section(itm, torch, dev, conf_frames)
 
-    cpu = None
+    cpu = cpu_mt = None
     if cpu_frames is not None:
         cpu = cpu_oracle_sample(cpu_frames, stride=cpu_stride, name=args.workload)
         cpu = {k: v for k, v in cpu.items() if k != "seconds"}
+        try:
+            cpu_mt = cpu_oracle_sample(cpu_frames, stride=cpu_stride, budget_s=15.0, name=args.workload,
+                                       threaded=True)
+            cpu_mt = {k: v for k, v in cpu_mt.items() if k != "seconds"}
+        except Exception as e:  # no OpenMP build on this host
+            cpu_mt = {"unavailable": "%s: %s" % (type(e).__name__, e)}
 
     if rank != 0:
         return
@@ -982,6 +1007,7 @@ def run_ours(args, world, rank, local):
             "launch_ms_mean": integ_ms / args.steps,
         },
         "cpu_baseline": cpu,
+        "cpu_baseline_threaded": cpu_mt,
         "clocks": clocks,
         "e2e": e2e,
         "gpu_launches": 5 * args.steps,  # enumerate (+ u16), commit (+ overflow), visible + range, integrate, raycast

@@ -6,6 +6,8 @@ bench's CPU-baseline leg are the only callers.  The product path never
 imports this package.  The arithmetic lives in ``itm_oracle.c`` (plain C,
 single-threaded, fp32 with every operation rounded separately, as the paper's
 listings are written in float); this module only marshals numpy arrays.
+``Scene(..., threaded=True)`` runs the same source built with OpenMP (the
+multi-threaded CPU baseline), whose results are identical.
 
 Every function here is pinned by tests in ``tests/test_oracle_pins.py``,
 ``tests/test_oracle_conf_pins.py``, ``tests/test_oracle_combined_pins.py``,
@@ -25,6 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "itm_oracle.c")
 _LIB_DIR = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_LIB_DIR, "liboracle.so")
+_LIB_MT = os.path.join(_LIB_DIR, "liboracle_omp.so")
 
 CFLAGS = ["-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared"]
 
@@ -33,24 +36,49 @@ ST_VBA_FULL = 2
 ST_RANGE = 4
 
 
+def _compile(out: str, extra, force: bool) -> str:
+    os.makedirs(_LIB_DIR, exist_ok=True)
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(_SRC):
+        tmp = out + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", *CFLAGS, *extra, "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, out)
+    return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction) into oracle/_build."""
-    os.makedirs(_LIB_DIR, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
-        tmp = _LIB + ".%d.tmp" % os.getpid()
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
-        os.replace(tmp, _LIB)
-    return _LIB
+    return _compile(_LIB, [], force)
+
+
+def build_threaded(force: bool = False) -> str:
+    """The same source with OpenMP (liboracle_omp.so)."""
+    return _compile(_LIB_MT, ["-fopenmp"], force)
 
 
 _lib = None
+_lib_mt = None
 
 
 def _load():
     global _lib
-    if _lib is not None:
-        return _lib
-    lib = ctypes.CDLL(build())
+    if _lib is None:
+        _lib = _bind(ctypes.CDLL(build()))
+    return _lib
+
+
+def _load_threaded():
+    global _lib_mt
+    if _lib_mt is None:
+        _lib_mt = _bind(ctypes.CDLL(build_threaded()))
+    return _lib_mt
+
+
+def threads() -> int:
+    """Threads the OpenMP build runs its parallel loops with."""
+    return int(_load_threaded().orc_threads())
+
+
+def _bind(lib):
     P = ctypes.c_void_p
     f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
     i16p = np.ctypeslib.ndpointer(np.int16, flags="C_CONTIGUOUS")
@@ -125,7 +153,8 @@ def _load():
     lib.orc_colour_at.argtypes = [P, f32p, ctypes.c_longlong, u8p]
     lib.orc_export_colour.restype = I
     lib.orc_export_colour.argtypes = [P, i16p, u8p, I]
-    _lib = lib
+    lib.orc_threads.restype = I
+    lib.orc_threads.argtypes = []
     return lib
 
 
@@ -148,8 +177,8 @@ class Scene:
     """One hashed TSDF volume held by the oracle."""
 
     def __init__(self, voxel_size, mu, max_w, num_buckets, num_excess, num_blocks,
-                 z_min, z_max, **_ignored):
-        lib = _load()
+                 z_min, z_max, threaded=False, **_ignored):
+        lib = self._lib = _load_threaded() if threaded else _load()
         self.p = lib.orc_scene_new(voxel_size, mu, int(max_w), int(num_buckets), int(num_excess),
                                    int(num_blocks), z_min, z_max)
         if not self.p:
@@ -159,13 +188,13 @@ class Scene:
 
     def __del__(self):
         if getattr(self, "p", None):
-            _load().orc_scene_free(self.p)
+            self._lib.orc_scene_free(self.p)
             self.p = None
 
     def allocate(self, depth, intr, T_wc) -> int:
         d = _f32(depth)
         H, W = d.shape
-        return _load().orc_allocate(self.p, d, W, H, _f32(intr), _f32(T_wc).ravel())
+        return self._lib.orc_allocate(self.p, d, W, H, _f32(intr), _f32(T_wc).ravel())
 
     def integrate(self, depth, intr, T_wc, wpx=None) -> int:
         d = _f32(depth)
@@ -175,12 +204,12 @@ class Scene:
             wpx = _f32(wpx)
             assert wpx.shape == d.shape
             wp = wpx.ctypes.data
-        return int(_load().orc_integrate(self.p, d, W, H, _f32(intr), _f32(T_wc).ravel(), wp))
+        return int(self._lib.orc_integrate(self.p, d, W, H, _f32(intr), _f32(T_wc).ravel(), wp))
 
     def raycast(self, W, H, intr, T_wc):
         vtx = np.zeros((H, W, 4), dtype=np.float32)
         nrm = np.zeros((H, W, 4), dtype=np.float32)
-        _load().orc_raycast(self.p, W, H, _f32(intr), _f32(T_wc).ravel(), vtx, nrm)
+        self._lib.orc_raycast(self.p, W, H, _f32(intr), _f32(T_wc).ravel(), vtx, nrm)
         return vtx, nrm
 
     def process(self, depth, intr, T_wc, raycast=True, wpx=None):
@@ -192,15 +221,15 @@ class Scene:
 
     @property
     def status(self) -> int:
-        return _load().orc_status(self.p)
+        return self._lib.orc_status(self.p)
 
     @property
     def num_allocated(self) -> int:
-        return _load().orc_num_allocated(self.p)
+        return self._lib.orc_num_allocated(self.p)
 
     @property
     def excess_used(self) -> int:
-        return _load().orc_excess_used(self.p)
+        return self._lib.orc_excess_used(self.p)
 
     def export(self, with_voxels=True):
         """(coords int16 [n,3], sdf float32 [n,512], w float32 [n,512]) in
@@ -209,27 +238,27 @@ class Scene:
         coords = np.zeros((n, 3), dtype=np.int16)
         sdf = np.zeros((n, 512), dtype=np.float32) if with_voxels else None
         w = np.zeros((n, 512), dtype=np.float32) if with_voxels else None
-        _load().orc_export(self.p, coords, sdf.ctypes.data if with_voxels else None,
+        self._lib.orc_export(self.p, coords, sdf.ctypes.data if with_voxels else None,
                            w.ctypes.data if with_voxels else None, n)
         return coords, sdf, w
 
     def entries(self) -> np.ndarray:
         nb, ne = self.params["num_buckets"], self.params["num_excess"]
         out = np.zeros((nb + ne, 5), dtype=np.int32)
-        _load().orc_entries(self.p, out)
+        self._lib.orc_entries(self.p, out)
         return out
 
     def mesh(self):
         """Marching-Cubes triangles of the zero level set: float32 [n, 3, 3]
         (three world-space vertices each, counter-clockwise seen from F > 0)."""
-        n = int(_load().orc_mesh(self.p, None, 0))
+        n = int(self._lib.orc_mesh(self.p, None, 0))
         out = np.zeros((max(n, 1), 3, 3), dtype=np.float32)
-        _load().orc_mesh(self.p, out.ctypes.data, n)
+        self._lib.orc_mesh(self.p, out.ctypes.data, n)
         return out[:n]
 
     # Sec. 3.1 colour voxels (readings in itm_oracle.c at colour_update)
     def colour_enable(self):
-        if _load().orc_colour_enable(self.p) != 0:
+        if self._lib.orc_colour_enable(self.p) != 0:
             raise ValueError("colour already on")
 
     def integrate_colour(self, depth, intr, T_wc, rgb, intr_c, T_d2c=None) -> int:
@@ -241,7 +270,7 @@ class Scene:
         rgb = np.ascontiguousarray(rgb, dtype=np.uint8)
         Hc, Wc = rgb.shape[:2]
         T = np.eye(4, dtype=np.float32) if T_d2c is None else _f32(T_d2c)
-        n = _load().orc_integrate_colour(self.p, d, W, H, _f32(intr), _f32(T_wc).ravel(), rgb.ravel(), Wc, Hc,
+        n = self._lib.orc_integrate_colour(self.p, d, W, H, _f32(intr), _f32(T_wc).ravel(), rgb.ravel(), Wc, Hc,
                                          _f32(intr_c), _f32(T).ravel())
         if n < 0:
             raise ValueError("colour is off")
@@ -252,7 +281,7 @@ class Scene:
         point (x, y, z, valid) of pts (float32 [..., 4])."""
         p = _f32(pts)
         out = np.zeros(p.shape[:-1] + (4,), dtype=np.uint8)
-        _load().orc_colour_at(self.p, p.reshape(-1), p.size // 4, out.reshape(-1))
+        self._lib.orc_colour_at(self.p, p.reshape(-1), p.size // 4, out.reshape(-1))
         return out
 
     def export_colour(self):
@@ -260,32 +289,32 @@ class Scene:
         n = self.num_allocated
         coords = np.zeros((max(n, 1), 3), dtype=np.int16)
         rgbw = np.zeros((max(n, 1), 512, 4), dtype=np.uint8)
-        _load().orc_export_colour(self.p, coords, rgbw.reshape(-1), n)
+        self._lib.orc_export_colour(self.p, coords, rgbw.reshape(-1), n)
         return coords[:n], rgbw[:n]
 
     # Sec. 5 swapping (readings in itm_oracle.c above orc_swap_enable)
     SW_HOST, SW_MERGE = 1, 2
 
     def swap_enable(self, transfer_blocks, idle_frames=1):
-        if _load().orc_swap_enable(self.p, int(transfer_blocks), int(idle_frames)) != 0:
+        if self._lib.orc_swap_enable(self.p, int(transfer_blocks), int(idle_frames)) != 0:
             raise ValueError("swapping already on or invalid arguments")
 
     def swap_in(self) -> int:
-        return int(_load().orc_swap_in(self.p))
+        return int(self._lib.orc_swap_in(self.p))
 
     def swap_out(self) -> int:
-        return int(_load().orc_swap_out(self.p))
+        return int(self._lib.orc_swap_out(self.p))
 
     def swap_counters(self) -> dict:
         out = np.zeros(5, dtype=np.int64)
-        _load().orc_swap_counters(self.p, out)
+        self._lib.orc_swap_counters(self.p, out)
         return dict(host_data=int(out[0]), swapped_out=int(out[1]), waiting=int(out[2]),
                     moved_in=int(out[3]), moved_out=int(out[4]))
 
     def swap_export_host(self):
         """(coords int16 [n,3], sdf float32 [n,512], w float32 [n,512], state
         int32 [n]) of the blocks with host data, in entry order."""
-        lib = _load()
+        lib = self._lib
         n = int(lib.orc_swap_export_host(self.p, None, None, None, None, 0))
         coords = np.zeros((max(n, 1), 3), dtype=np.int16)
         sdf = np.zeros((max(n, 1), 512), dtype=np.float32)
@@ -298,11 +327,15 @@ class Scene:
         """Allocate block b (if missing) and set its 512 voxels (x + 8y + 64z)."""
         sdf = _f32(np.broadcast_to(np.asarray(sdf, dtype=np.float32), (512,)))
         w = _f32(np.broadcast_to(np.asarray(w, dtype=np.float32), (512,)))
-        if _load().orc_set_block(self.p, int(b[0]), int(b[1]), int(b[2]), sdf, w) != 0:
+        if self._lib.orc_set_block(self.p, int(b[0]), int(b[1]), int(b[2]), sdf, w) != 0:
             raise RuntimeError("block could not be allocated")
 
 
 # ------------------------------------------------------------- combined map
+
+def _lib_of(scenes):
+    return scenes[0]._lib if scenes else _load()
+
 
 def _scene_array(scenes):
     arr = (ctypes.c_void_p * max(1, len(scenes)))(*[sc.p for sc in scenes])
@@ -319,7 +352,7 @@ def combined_value(scenes, P, X):
     submap-from-world poses P (n x 4 x 4): (value, weight sum)."""
     n = len(scenes)
     den = ctypes.c_float(0.0)
-    v = _load().orc_combined_value(_scene_array(scenes), _poses(P, n), n, _f32(X), ctypes.byref(den))
+    v = _lib_of(scenes).orc_combined_value(_scene_array(scenes), _poses(P, n), n, _f32(X), ctypes.byref(den))
     return float(v), float(den.value)
 
 
@@ -328,8 +361,8 @@ def raycast_combined(scenes, P, W, H, intr, T_wc):
     n = len(scenes)
     vtx = np.zeros((H, W, 4), dtype=np.float32)
     nrm = np.zeros((H, W, 4), dtype=np.float32)
-    _load().orc_raycast_combined(_scene_array(scenes), _poses(P, n) if n else np.zeros(16, np.float32), n, W, H,
-                                 _f32(intr), _f32(T_wc).ravel(), vtx, nrm)
+    _lib_of(scenes).orc_raycast_combined(_scene_array(scenes), _poses(P, n) if n else np.zeros(16, np.float32),
+                                         n, W, H, _f32(intr), _f32(T_wc).ravel(), vtx, nrm)
     return vtx, nrm
 
 

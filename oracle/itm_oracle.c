@@ -10,6 +10,11 @@
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fno-fast-math -shared -fPIC
  * (no FMA contraction: every float operation below is rounded on its own, in
  * the order written, which is what makes the integer decisions reproducible).
+ * The same source built with -fopenmp is the multi-threaded CPU baseline:
+ * integration runs over blocks and the raycast over image rows in parallel
+ * (each voxel and each pixel is computed alone, so nothing changes), and the
+ * allocation records each row's blocks in parallel and inserts them afterwards
+ * in the single-threaded order, so the hash table comes out byte-identical.
  *
  * What each function follows:
  *   orc_hash_index        Sec. 3.2, the printed hashIndex function
@@ -57,6 +62,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_BLOCK 8
 #define ORC_BLOCK3 512
@@ -298,9 +306,37 @@ static int in_i16(int v) { return v >= -32768 && v <= 32767; }
 
 /* -------------------------------------------------------------- allocation */
 
+/* Where the blocks a segment crosses go: NULL inserts each into the scene at
+ * once; a list records them (with the status bits they raised) so that they
+ * can be inserted later in the same order. */
+typedef struct {
+    int16_t *xyz;
+    int n, cap;
+    int status;
+} block_list;
+
+static void emit_block(orc_scene *s, block_list *out, int bx, int by, int bz)
+{
+    if (!out) {
+        insert_if_missing(s, bx, by, bz);
+        return;
+    }
+    if (out->n == out->cap) {
+        int cap = out->cap ? 2 * out->cap : 1024;
+        int16_t *p = (int16_t *)realloc(out->xyz, (size_t)cap * 3 * sizeof(int16_t));
+        if (!p) abort();
+        out->xyz = p;
+        out->cap = cap;
+    }
+    out->xyz[3 * out->n + 0] = (int16_t)bx;
+    out->xyz[3 * out->n + 1] = (int16_t)by;
+    out->xyz[3 * out->n + 2] = (int16_t)bz;
+    out->n += 1;
+}
+
 /* Blocks crossed by the segment q0 -> q1 (block units), stepping one axis at a
  * time towards the end block; ties go to x, then y, then z. */
-static void dda_blocks(orc_scene *s, const float q0[3], const float q1[3])
+static void dda_blocks(orc_scene *s, block_list *out, const float q0[3], const float q1[3])
 {
     int cur[3], end[3], step[3], left[3];
     float tmax[3], tdelta[3];
@@ -308,7 +344,8 @@ static void dda_blocks(orc_scene *s, const float q0[3], const float q1[3])
         float f0 = floorf(q0[i]);
         float f1 = floorf(q1[i]);
         if (!(f0 >= -32768.0f && f0 <= 32767.0f && f1 >= -32768.0f && f1 <= 32767.0f)) {
-            s->status |= ORC_ST_RANGE;
+            if (out) out->status |= ORC_ST_RANGE;
+            else s->status |= ORC_ST_RANGE;
             return;
         }
         cur[i] = (int)f0;
@@ -331,7 +368,7 @@ static void dda_blocks(orc_scene *s, const float q0[3], const float q1[3])
             tmax[i] = 0.0f;
         }
     }
-    insert_if_missing(s, cur[0], cur[1], cur[2]);
+    emit_block(s, out, cur[0], cur[1], cur[2]);
     while (left[0] + left[1] + left[2] > 0) {
         int a = -1;
         for (int i = 0; i < 3; ++i)
@@ -339,8 +376,33 @@ static void dda_blocks(orc_scene *s, const float q0[3], const float q1[3])
         cur[a] += step[a];
         tmax[a] = tmax[a] + tdelta[a];
         left[a] -= 1;
-        insert_if_missing(s, cur[0], cur[1], cur[2]);
+        emit_block(s, out, cur[0], cur[1], cur[2]);
     }
+}
+
+/* Sec. 4.2, first part, for pixel (u, v): the ends of the line from depth
+ * d-mu to d+mu on the pixel's ray, in block units.  Returns 0 when the pixel
+ * has no measurement in [z_min, z_max]. */
+static int pixel_segment(const orc_scene *s, const float *depth, int W, int u, int v, const float intr[4],
+                         const float T_wc[16], float inv_b, float q0[3], float q1[3])
+{
+    const float fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3];
+    const float mu = s->mu;
+    float d = depth[(size_t)v * W + u];
+    if (!(d > 0.0f)) return 0;
+    if (d < s->z_min || d > s->z_max) return 0;
+    float rx = ((float)u - cx) / fx;
+    float ry = ((float)v - cy) / fy;
+    float z0 = d - mu;
+    float z1 = d + mu;
+    if (z0 < 1e-3f) z0 = 1e-3f;
+    for (int i = 0; i < 3; ++i) {
+        float p0 = row_apply(&T_wc[4 * i], rx * z0, ry * z0, z0);
+        float p1 = row_apply(&T_wc[4 * i], rx * z1, ry * z1, z1);
+        q0[i] = p0 * inv_b;
+        q1[i] = p1 * inv_b;
+    }
+    return 1;
 }
 
 /* Sec. 4.2, first and second parts: for each valid pixel, the line from
@@ -350,31 +412,46 @@ static void dda_blocks(orc_scene *s, const float q0[3], const float q1[3])
 int orc_allocate(orc_scene *s, const float *depth, int W, int H, const float intr[4],
                  const float T_wc[16])
 {
-    const float fx = intr[0], fy = intr[1], cx = intr[2], cy = intr[3];
     const float inv_b = (float)(1.0 / (8.0 * (double)s->voxel_size));
-    const float mu = s->mu;
     if (s->swap_on) ++s->frame;
+#ifndef _OPENMP
     for (int v = 0; v < H; ++v) {
         for (int u = 0; u < W; ++u) {
-            float d = depth[(size_t)v * W + u];
-            if (!(d > 0.0f)) continue;
-            if (d < s->z_min || d > s->z_max) continue;
-            float rx = ((float)u - cx) / fx;
-            float ry = ((float)v - cy) / fy;
-            float z0 = d - mu;
-            float z1 = d + mu;
-            if (z0 < 1e-3f) z0 = 1e-3f;
             float q0[3], q1[3];
-            for (int i = 0; i < 3; ++i) {
-                float p0 = row_apply(&T_wc[4 * i], rx * z0, ry * z0, z0);
-                float p1 = row_apply(&T_wc[4 * i], rx * z1, ry * z1, z1);
-                q0[i] = p0 * inv_b;
-                q1[i] = p1 * inv_b;
-            }
-            dda_blocks(s, q0, q1);
+            if (pixel_segment(s, depth, W, u, v, intr, T_wc, inv_b, q0, q1)) dda_blocks(s, NULL, q0, q1);
         }
     }
+#else
+    /* the crossed blocks of each row, found in parallel, then inserted in
+     * row-major order: the insertions and their order are those above */
+    block_list *rows = (block_list *)calloc((size_t)(H > 0 ? H : 1), sizeof(block_list));
+    if (!rows) abort();
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int v = 0; v < H; ++v) {
+        for (int u = 0; u < W; ++u) {
+            float q0[3], q1[3];
+            if (pixel_segment(s, depth, W, u, v, intr, T_wc, inv_b, q0, q1)) dda_blocks(s, &rows[v], q0, q1);
+        }
+    }
+    for (int v = 0; v < H; ++v) {
+        for (int i = 0; i < rows[v].n; ++i)
+            insert_if_missing(s, rows[v].xyz[3 * i], rows[v].xyz[3 * i + 1], rows[v].xyz[3 * i + 2]);
+        s->status |= rows[v].status;
+        free(rows[v].xyz);
+    }
+    free(rows);
+#endif
     return s->status;
+}
+
+/* Threads the parallel loops use: 1 in the plain build. */
+int orc_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* ------------------------------------------------------------- integration */
@@ -444,6 +521,7 @@ static long long integrate_impl(orc_scene *s, const float *depth, int W, int H, 
     const float max_w = (float)s->max_w;
     const float umax = (float)(W - 2), vmax = (float)(H - 2);
     long long updated = 0;
+#pragma omp parallel for reduction(+ : updated) schedule(dynamic, 16)
     for (int k = 0; k < s->n_alloc; ++k) {
         int ptr = s->alloc_order[k];
         int bx = s->block_pos[3 * ptr], by = s->block_pos[3 * ptr + 1], bz = s->block_pos[3 * ptr + 2];
@@ -629,6 +707,7 @@ int orc_raycast(const orc_scene *s, int W, int H, const float intr[4], const flo
     const float mu = s->mu;
     const int max_iter = (int)(4.0f * (s->z_max - s->z_min) / vs) + 64;
     int hits = 0;
+#pragma omp parallel for reduction(+ : hits) schedule(dynamic, 2)
     for (int v = 0; v < H; ++v) {
         for (int u = 0; u < W; ++u) {
             size_t o4 = 4 * ((size_t)v * W + u);
@@ -848,6 +927,7 @@ int orc_raycast_combined(const orc_scene *const *S, const float *P, int n, int W
     const float mu = s0->mu;
     const int max_iter = (int)(4.0f * (s0->z_max - s0->z_min) / vs) + 64;
     int hits = 0;
+#pragma omp parallel for reduction(+ : hits) schedule(dynamic, 2)
     for (int v = 0; v < H; ++v) {
         for (int u = 0; u < W; ++u) {
             size_t o4 = 4 * ((size_t)v * W + u);
