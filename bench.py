@@ -284,15 +284,23 @@ def cpu_oracle_sample(frames, stride=30, budget_s=30.0, name="kinect", threaded=
     cores = oracle.threads() if threaded else 1
     ia = w.intr.as_array()
     done, t0, upd = 0, time.perf_counter(), 0
+    stage = [0.0, 0.0, 0.0]
     idx = sorted(frames)
     for k in idx:
         raw, T = frames[k]
+        ta = time.perf_counter()
         d = oracle.depth_u16_to_f32(raw)
         sc.allocate(d, ia, T)
+        tb = time.perf_counter()
         upd += sc.integrate(d, ia, T)
+        tc = time.perf_counter()
         sc.raycast(w.intr.width, w.intr.height, ia, T)
+        td = time.perf_counter()
+        stage[0] += tb - ta
+        stage[1] += tc - tb
+        stage[2] += td - tc
         done += 1
-        if time.perf_counter() - t0 > budget_s:
+        if td - t0 > budget_s:
             break
     dt = time.perf_counter() - t0
     return {"value": done / dt, "unit": "frames/s", "cores": cores, "kind": "oracle",
@@ -300,7 +308,9 @@ def cpu_oracle_sample(frames, stride=30, budget_s=30.0, name="kinect", threaded=
                       "u16->f32 + allocate + integrate over all allocated blocks + raycast, %s"
                       % (done, stride, WORKLOADS[name][0],
                          "OpenMP build, %d threads" % cores if threaded else "single thread"),
-            "voxel_updates_per_s": upd / dt, "seconds": dt, "host": host_cpu()}
+            "voxel_updates_per_s": upd / dt, "seconds": dt, "host": host_cpu(),
+            "stage_ms_mean": {"u16_to_f32_and_allocate": 1000 * stage[0] / done,
+                              "integrate": 1000 * stage[1] / done, "raycast": 1000 * stage[2] / done}}
 
 
 def run_reference(args, world, rank):
