@@ -1,10 +1,12 @@
 """The C ABI library loads and exports every function the header declares.
-No GPU calls: only symbol presence and the host-side hash function."""
+No GPU calls: symbol presence and the host-only functions (the hash function
+and the tracker's Gauss-Newton step)."""
 
 import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -71,3 +73,45 @@ def test_binding_knows_every_error_code_and_constant():
                  "ITM_MLP_SCRATCH_PER_SAMPLE", "ITM_BATCH_STAGES"):
         if name in defines and hasattr(itm, name):
             assert int(defines[name]) == getattr(itm, name), name
+
+
+def _icp_sums(rng, n=500, scale=1.0):
+    """Point-to-plane sums (layout of itm_icp_reduce) of n random rows."""
+    J = rng.normal(size=(n, 6)) * scale
+    r = rng.normal(size=n) * 1e-3
+    H = J.T @ J
+    iu = np.triu_indices(6)
+    return np.concatenate([H[iu], J.T @ r, [r @ r, n]])
+
+
+def test_host_icp_step_equals_oracle():
+    """itm_icp_step is host code: its Cholesky solve and pose update equal
+    the oracle's Gauss-Newton step on random systems, and it refuses the
+    systems without a unique solution (fewer than 6 pixels, a rank-deficient
+    H)."""
+    import oracle
+    import paper_1708_00783_gb300 as itm
+    from tests.test_oracle_track_pins import exp_pose
+    rng = np.random.default_rng(21)
+    for k in range(20):
+        T = exp_pose(rng.normal(size=6) * 0.3, np.eye(4)).astype(np.float32)
+        s = _icp_sums(rng, scale=10.0 ** rng.uniform(-2, 1))
+        T1, x1 = itm.itm_icp_step(s, T)
+        T2, x2, ok = oracle.icp_update(s, T)
+        assert ok
+        np.testing.assert_allclose(x1, x2, rtol=1e-9, atol=1e-12)
+        np.testing.assert_allclose(T1, T2, atol=2e-7)
+    s = _icp_sums(rng)
+    few = s.copy()
+    few[28] = 5.0
+    flat = _icp_sums(rng)
+    J = rng.normal(size=(100, 6))
+    J[:, 5] = 0.0  # no constraint on the z translation
+    iu = np.triu_indices(6)
+    flat[:21] = (J.T @ J)[iu]
+    for bad in (few, flat):
+        with pytest.raises(itm.ItmError):
+            itm.itm_icp_step(bad, T)
+    # the oracle takes the pixel-count rule in its tracking loop, before the
+    # step; the step itself refuses only the rank-deficient system
+    assert not oracle.icp_update(flat, T)[2]
