@@ -25,7 +25,8 @@ ITM_OK = 0
 ERRORS = {1: "ITM_ERR_ARG", 2: "ITM_ERR_CUDA", 3: "ITM_ERR_HASH_FULL", 4: "ITM_ERR_VBA_FULL",
           5: "ITM_ERR_RANGE", 6: "ITM_ERR_TIMEOUT", 7: "ITM_ERR_OVERFLOW", 8: "ITM_ERR_TOO_LARGE",
           9: "ITM_ERR_SINGULAR", 10: "ITM_ERR_BOUNDS"}
-ITM_ERR_TOO_LARGE = 8
+(ITM_ERR_ARG, ITM_ERR_CUDA, ITM_ERR_HASH_FULL, ITM_ERR_VBA_FULL, ITM_ERR_RANGE, ITM_ERR_TIMEOUT, ITM_ERR_OVERFLOW,
+ ITM_ERR_TOO_LARGE, ITM_ERR_SINGULAR, ITM_ERR_BOUNDS) = range(1, 11)
 ITM_NOALLOC_MAX_BLOCKS = 1 << 21
 ITM_MLP_FEATURES, ITM_MLP_HIDDEN, ITM_MLP_PARAMS = 52, 64, 7617
 ITM_MLP_PACKED_BYTES, ITM_MLP_SCRATCH_PER_SAMPLE = 17168, 257

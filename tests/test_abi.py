@@ -68,6 +68,7 @@ def test_binding_knows_every_error_code_and_constant():
     text = open(os.path.join(ROOT, "include", "itm.h")).read()
     codes = {int(v): n for n, v in re.findall(r"(ITM_ERR_[A-Z_]+)\s*=\s*(\d+)", text)}
     assert codes and codes == itm.ERRORS
+    assert all(getattr(itm, n) == v for v, n in codes.items())
     defines = dict(re.findall(r"#define\s+(ITM_[A-Z0-9_]+)\s+\(?([0-9]+)", text))
     for name in ("ITM_MLP_FEATURES", "ITM_MLP_HIDDEN", "ITM_MLP_PARAMS", "ITM_MLP_PACKED_BYTES",
                  "ITM_MLP_SCRATCH_PER_SAMPLE", "ITM_BATCH_STAGES"):
@@ -115,3 +116,57 @@ def test_host_icp_step_equals_oracle():
     # the oracle takes the pixel-count rule in its tracking loop, before the
     # step; the step itself refuses only the rank-deficient system
     assert not oracle.icp_update(flat, T)[2]
+
+
+_NULL_CHILD = r'''
+import ctypes, re, sys
+import paper_1708_00783_gb300 as itm
+text = re.sub(r"/\*.*?\*/", "", open(sys.argv[1]).read(), flags=re.S)
+for name in sorted(set(re.findall(r"\b(itm_[a-z0-9_]+)\s*\(", text))):
+    if name in ("itm_version", "itm_hash_index", "itm_track_scratch_bytes"):
+        continue
+    f = getattr(itm._lib, name)
+    args = [None if (a is ctypes.c_void_p or issubclass(a, ctypes._Pointer)) else a(0) for a in f.argtypes]
+    print(name, f(*args), flush=True)
+'''
+
+
+def test_null_arguments_rejected_before_any_device_call():
+    """Every call that takes a scene, a buffer or a pointer answers NULL /
+    zero arguments with ITM_ERR_ARG from its host-side checks, before any
+    CUDA call (this host has no GPU); a zero-length depth conversion is an
+    empty no-op.  Run in a child process so a crash would fail the test, not
+    end the session."""
+    import subprocess
+    import sys
+    import paper_1708_00783_gb300 as itm
+    r = subprocess.run([sys.executable, "-c", _NULL_CHILD, os.path.join(ROOT, "include", "itm.h")],
+                       capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stdout[-400:] + r.stderr[-400:]
+    got = dict(ln.split() for ln in r.stdout.splitlines())
+    assert len(got) == len(header_functions()) - 3
+    for name, code in got.items():
+        want = itm.ITM_OK if name == "itm_depth_u16_to_f32" else itm.ITM_ERR_ARG
+        assert int(code) == want, (name, code)
+
+
+def test_scene_parameters_checked_on_the_host():
+    """itm_scene_create refuses each invalid parameter with ITM_ERR_ARG
+    before allocating anything."""
+    import paper_1708_00783_gb300 as itm
+    base = dict(voxel_size=0.005, mu=0.02, max_w=100, num_buckets=1 << 10, num_excess=64, num_blocks=256,
+                z_min=0.4, z_max=5.0, weight_mode=0)
+    bad = [dict(voxel_size=0.0), dict(voxel_size=float("nan")), dict(mu=-0.01), dict(weight_mode=2),
+           dict(max_w=0), dict(max_w=256), dict(num_buckets=1000), dict(num_buckets=0), dict(num_excess=-1),
+           dict(num_blocks=-1), dict(num_blocks=(1 << 24) + 1), dict(z_min=0.0), dict(z_max=0.4)]
+    for change in bad:
+        p = itm.itm_scene_params(**dict(base, **change))
+        out = ctypes.c_void_p()
+        assert itm._lib.itm_scene_create(ctypes.byref(p), ctypes.byref(out)) == itm.ITM_ERR_ARG, change
+        assert not out.value
+    # the learned mode keeps float weights, so its cap may exceed 255
+    import torch
+    if not torch.cuda.is_available():
+        p = itm.itm_scene_params(**dict(base, weight_mode=1, max_w=1000))
+        out = ctypes.c_void_p()
+        assert itm._lib.itm_scene_create(ctypes.byref(p), ctypes.byref(out)) == itm.ITM_ERR_CUDA
