@@ -1,6 +1,7 @@
 """The C ABI library loads and exports every function the header declares.
-No GPU calls: symbol presence and the host-only functions (the hash function
-and the tracker's Gauss-Newton step)."""
+No GPU calls: symbol presence, the host-only functions (the hash function and
+the tracker's Gauss-Newton step) and the argument checks every call makes on
+the host before it touches the device."""
 
 import ctypes
 import os
