@@ -542,8 +542,49 @@ def itm_swap_export_host(scene, weight_mode=0):
     return coords[:cnt], sdf[:cnt], w[:cnt].astype(np.float32), st[:cnt]
 
 
+def _buffer(x, dtype, count, what):
+    """A buffer on its way to the device: a contiguous CUDA tensor of `dtype`
+    with at least `count` elements (None, or a raw device address given as an
+    int, passes as is).  Anything else raises ItmError(ITM_ERR_ARG) before a
+    pointer reaches a kernel."""
+    if x is None or isinstance(x, int):
+        return x
+    import torch
+    why = None
+    if not isinstance(x, torch.Tensor):
+        why = "a CUDA tensor is needed, not %s" % type(x).__name__
+    elif not x.is_cuda:
+        why = "the tensor is on %s, not on a CUDA device" % x.device
+    elif x.dtype != dtype:
+        why = "dtype %s, expected %s" % (x.dtype, dtype)
+    elif not x.is_contiguous():
+        why = "the tensor is not contiguous"
+    elif x.numel() < count:
+        why = "%d elements, at least %d needed" % (x.numel(), count)
+    if why:
+        raise ItmError(ITM_ERR_ARG, "%s (%s)" % (what, why))
+    return x
+
+
+def _f32_t():
+    import torch
+    return torch.float32
+
+
+def _u8_t():
+    import torch
+    return torch.uint8
+
+
+def _pixels(intr):
+    return max(0, int(getattr(intr, "width", 0))) * max(0, int(getattr(intr, "height", 0)))
+
+
 class Scene:
-    """Owning wrapper of an itm_scene handle."""
+    """Owning wrapper of an itm_scene handle.  Its methods take torch CUDA
+    tensors (float32 depth [H, W] and maps [H, W, 4], uint8 RGB [Hc, Wc, 3])
+    and check device, dtype, contiguity and size against the intrinsics
+    before calling the library."""
 
     def __init__(self, voxel_size, mu, max_w, num_buckets, num_excess, num_blocks, z_min, z_max,
                  weight_mode=0, **_ignored):
@@ -567,18 +608,26 @@ class Scene:
         itm_scene_reset(self.handle, stream)
 
     def allocate(self, depth, intr, T_wc, stream=None):
+        _buffer(depth, _f32_t(), _pixels(intr), "Scene.allocate: depth")
         itm_allocate(self.handle, depth, intr, T_wc, stream)
 
     def integrate(self, depth, intr, T_wc, stream=None, wpx=None):
+        _buffer(depth, _f32_t(), _pixels(intr), "Scene.integrate: depth")
+        _buffer(wpx, _f32_t(), _pixels(intr), "Scene.integrate: wpx")
         if wpx is None:
             itm_integrate(self.handle, depth, intr, T_wc, stream)
         else:
             itm_integrate_weighted(self.handle, depth, wpx, intr, T_wc, stream)
 
     def raycast(self, intr, T_wc, vertex, normal, stream=None):
+        _buffer(vertex, _f32_t(), 4 * _pixels(intr), "Scene.raycast: vertex")
+        _buffer(normal, _f32_t(), 4 * _pixels(intr), "Scene.raycast: normal")
         itm_raycast(self.handle, intr, T_wc, vertex, normal, stream)
 
     def process(self, depth, intr, T_wc, vertex=None, normal=None, stream=None):
+        _buffer(depth, _f32_t(), _pixels(intr), "Scene.process: depth")
+        _buffer(vertex, _f32_t(), 4 * _pixels(intr), "Scene.process: vertex")
+        _buffer(normal, _f32_t(), 4 * _pixels(intr), "Scene.process: normal")
         itm_process_frame(self.handle, depth, intr, T_wc, vertex, normal, stream)
 
     def stats(self) -> dict:
@@ -594,9 +643,16 @@ class Scene:
         itm_colour_enable(self.handle)
 
     def integrate_colour(self, depth, intr, T_wc, rgb, intr_colour, T_d2c=None, stream=None):
+        _buffer(depth, _f32_t(), _pixels(intr), "Scene.integrate_colour: depth")
+        _buffer(rgb, _u8_t(), 3 * _pixels(intr_colour), "Scene.integrate_colour: rgb")
         itm_integrate_colour(self.handle, depth, intr, T_wc, rgb, intr_colour, T_d2c, stream)
 
     def colour_at(self, points, out, stream=None):
+        _buffer(points, _f32_t(), 0, "Scene.colour_at: points")
+        n = points.numel() if hasattr(points, "numel") else 0
+        if n % 4:
+            raise ItmError(ITM_ERR_ARG, "Scene.colour_at: points (not a multiple of 4 floats)")
+        _buffer(out, _u8_t(), n, "Scene.colour_at: out")
         itm_colour_at(self.handle, points, out, stream)
 
     def export_colour(self):

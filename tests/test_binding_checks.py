@@ -1,0 +1,98 @@
+"""The Scene wrapper checks every buffer before it calls the library (CPU).
+
+A host tensor, a numpy array, the wrong dtype, a strided view or a buffer
+smaller than the intrinsics ask for raises ItmError(ITM_ERR_ARG) in Python,
+so no such pointer reaches a kernel; valid buffers pass through unchanged.
+The library calls are replaced by stubs here, and a tensor subclass stands in
+for a CUDA tensor (this host has no GPU).
+"""
+
+import numpy as np
+import pytest
+import torch
+
+import paper_1708_00783_gb300 as itm
+
+
+class FakeCuda(torch.Tensor):
+    @property
+    def is_cuda(self):
+        return True
+
+
+def cuda_like(*shape, dtype=torch.float32):
+    return torch.zeros(*shape, dtype=dtype).as_subclass(FakeCuda)
+
+
+CALLS = ("itm_allocate", "itm_integrate", "itm_integrate_weighted", "itm_raycast", "itm_process_frame",
+         "itm_integrate_colour", "itm_colour_at")
+
+
+@pytest.fixture()
+def scene(monkeypatch):
+    reached = []
+    for name in CALLS:
+        monkeypatch.setattr(itm, name, lambda *a, _n=name, **k: reached.append(_n))
+    sc = object.__new__(itm.Scene)
+    sc.handle = 1
+    sc.params = {}
+    sc.reached = reached
+    yield sc
+    sc.handle = None
+
+
+H, W = 12, 16
+INTR = itm.make_intrinsics(W, H, 20.0, 20.0, 7.5, 5.5)
+T = np.eye(4)
+
+
+def test_valid_buffers_reach_the_library(scene):
+    d = cuda_like(H, W)
+    v, n = cuda_like(H, W, 4), cuda_like(H, W, 4)
+    scene.allocate(d, INTR, T)
+    scene.integrate(d, INTR, T)
+    scene.integrate(d, INTR, T, wpx=cuda_like(H, W))
+    scene.raycast(INTR, T, v, n)
+    scene.process(d, INTR, T)
+    scene.process(d, INTR, T, v, n)
+    scene.integrate_colour(d, INTR, T, cuda_like(H, W, 3, dtype=torch.uint8), INTR)
+    scene.colour_at(v, cuda_like(H, W, 4, dtype=torch.uint8))
+    scene.allocate(123456, INTR, T)  # a raw device address passes as is
+    assert scene.reached == ["itm_allocate", "itm_integrate", "itm_integrate_weighted", "itm_raycast",
+                             "itm_process_frame", "itm_process_frame", "itm_integrate_colour", "itm_colour_at",
+                             "itm_allocate"]
+
+
+@pytest.mark.parametrize("bad, why", [
+    (torch.zeros(H, W), "not on a CUDA device"),
+    (np.zeros((H, W), np.float32), "CUDA tensor is needed"),
+    (cuda_like(H, W, dtype=torch.float64), "dtype"),
+    (cuda_like(W, 2 * H)[:, ::2], "not contiguous"),
+    (cuda_like(H, W - 1), "at least"),
+])
+def test_bad_depth_refused_before_the_library(scene, bad, why):
+    for call in (lambda: scene.allocate(bad, INTR, T), lambda: scene.integrate(bad, INTR, T),
+                 lambda: scene.process(bad, INTR, T)):
+        with pytest.raises(itm.ItmError, match=why) as e:
+            call()
+        assert e.value.code == itm.ITM_ERR_ARG
+    assert scene.reached == []
+
+
+def test_bad_maps_and_colour_buffers_refused(scene):
+    d, v = cuda_like(H, W), cuda_like(H, W, 4)
+    cases = [
+        lambda: scene.raycast(INTR, T, cuda_like(H, W, 3), v),               # vertex map too small
+        lambda: scene.raycast(INTR, T, v, torch.zeros(H, W, 4)),             # normal map on the host
+        lambda: scene.process(d, INTR, T, v, cuda_like(H, W, 4, dtype=torch.float16)),
+        lambda: scene.integrate(d, INTR, T, wpx=cuda_like(H, W, dtype=torch.uint8)),
+        lambda: scene.integrate_colour(d, INTR, T, cuda_like(H, W, 3), INTR),  # float RGB
+        lambda: scene.integrate_colour(d, INTR, T, cuda_like(H, W, 2, dtype=torch.uint8), INTR),
+        lambda: scene.colour_at(cuda_like(5, 3), cuda_like(5, 4, dtype=torch.uint8)),  # 15 floats: no whole point
+        lambda: scene.colour_at(v, cuda_like(H, W, 2, dtype=torch.uint8)),
+    ]
+    for c in cases:
+        with pytest.raises(itm.ItmError) as e:
+            c()
+        assert e.value.code == itm.ITM_ERR_ARG
+    assert scene.reached == []
