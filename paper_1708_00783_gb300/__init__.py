@@ -190,6 +190,44 @@ def _pose(T):
     return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
 
 
+def _buffer(x, dtype, count, what):
+    """A buffer on its way to the device: a contiguous CUDA tensor of `dtype`
+    with at least `count` elements (None, or a raw device address given as an
+    int, passes as is).  Anything else raises ItmError(ITM_ERR_ARG) before a
+    pointer reaches a kernel."""
+    if x is None or isinstance(x, int):
+        return x
+    import torch
+    why = None
+    if not isinstance(x, torch.Tensor):
+        why = "a CUDA tensor is needed, not %s" % type(x).__name__
+    elif not x.is_cuda:
+        why = "the tensor is on %s, not on a CUDA device" % x.device
+    elif x.dtype != dtype:
+        why = "dtype %s, expected %s" % (x.dtype, dtype)
+    elif not x.is_contiguous():
+        why = "the tensor is not contiguous"
+    elif x.numel() < count:
+        why = "%d elements, at least %d needed" % (x.numel(), count)
+    if why:
+        raise ItmError(ITM_ERR_ARG, "%s (%s)" % (what, why))
+    return x
+
+
+def _f32_t():
+    import torch
+    return torch.float32
+
+
+def _u8_t():
+    import torch
+    return torch.uint8
+
+
+def _pixels(intr):
+    return max(0, int(getattr(intr, "width", 0))) * max(0, int(getattr(intr, "height", 0)))
+
+
 def make_intrinsics(width, height, fx, fy, cx, cy) -> itm_intrinsics:
     return itm_intrinsics(int(width), int(height), float(fx), float(fy), float(cx), float(cy))
 
@@ -439,6 +477,10 @@ def make_batch_items(items):
     items = list(items)
     arr = (itm_batch_item * len(items))()
     for k, (scene, depth, intr, T, vtx, nrm) in enumerate(items):
+        n = _pixels(intr)
+        _buffer(depth, _f32_t(), n, "batch item %d: depth" % k)
+        _buffer(vtx, _f32_t(), 4 * n, "batch item %d: vertex" % k)
+        _buffer(nrm, _f32_t(), 4 * n, "batch item %d: normal" % k)
         arr[k].scene = scene
         arr[k].depth_dev = _ptr(depth)
         arr[k].intr = intr
@@ -540,44 +582,6 @@ def itm_swap_export_host(scene, weight_mode=0):
     _check(_lib.itm_swap_export_host(scene, coords.ctypes.data, sdf.ctypes.data, w.ctypes.data, st.ctypes.data,
                                      cnt, ctypes.byref(n)), "itm_swap_export_host")
     return coords[:cnt], sdf[:cnt], w[:cnt].astype(np.float32), st[:cnt]
-
-
-def _buffer(x, dtype, count, what):
-    """A buffer on its way to the device: a contiguous CUDA tensor of `dtype`
-    with at least `count` elements (None, or a raw device address given as an
-    int, passes as is).  Anything else raises ItmError(ITM_ERR_ARG) before a
-    pointer reaches a kernel."""
-    if x is None or isinstance(x, int):
-        return x
-    import torch
-    why = None
-    if not isinstance(x, torch.Tensor):
-        why = "a CUDA tensor is needed, not %s" % type(x).__name__
-    elif not x.is_cuda:
-        why = "the tensor is on %s, not on a CUDA device" % x.device
-    elif x.dtype != dtype:
-        why = "dtype %s, expected %s" % (x.dtype, dtype)
-    elif not x.is_contiguous():
-        why = "the tensor is not contiguous"
-    elif x.numel() < count:
-        why = "%d elements, at least %d needed" % (x.numel(), count)
-    if why:
-        raise ItmError(ITM_ERR_ARG, "%s (%s)" % (what, why))
-    return x
-
-
-def _f32_t():
-    import torch
-    return torch.float32
-
-
-def _u8_t():
-    import torch
-    return torch.uint8
-
-
-def _pixels(intr):
-    return max(0, int(getattr(intr, "width", 0))) * max(0, int(getattr(intr, "height", 0)))
 
 
 class Scene:

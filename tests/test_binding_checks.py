@@ -96,3 +96,16 @@ def test_bad_maps_and_colour_buffers_refused(scene):
             c()
         assert e.value.code == itm.ITM_ERR_ARG
     assert scene.reached == []
+
+
+def test_batch_items_checked():
+    """make_batch_items (and so itm_batch_run given tuples) checks each
+    item's depth and map buffers the same way."""
+    d, v = cuda_like(H, W), cuda_like(H, W, 4)
+    arr = itm.make_batch_items([(1, d, INTR, T, v, cuda_like(H, W, 4)), (2, d, INTR, T, None, None)])
+    assert len(arr) == 2 and arr[1].vertex_dev is None
+    for bad in [(1, torch.zeros(H, W), INTR, T, v, v), (1, d, INTR, T, cuda_like(H, W), v),
+                (1, d, INTR, T, v, cuda_like(H, W, 4, dtype=torch.float64))]:
+        with pytest.raises(itm.ItmError) as e:
+            itm.make_batch_items([(2, d, INTR, T, None, None), bad])
+        assert e.value.code == itm.ITM_ERR_ARG and "batch item 1" in str(e.value)
