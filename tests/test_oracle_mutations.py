@@ -47,6 +47,27 @@ MUTANTS = [
      "                t = t - F * tmu;\n            }\n            float p[3];"),
     (CORE, "normal sign", "                float fm = trilinear(s, qm, &obs);\n                g[a] = fp - fm;",
      "                float fm = trilinear(s, qm, &obs);\n                g[a] = fm - fp;"),
+    (CORE, "no weight cap", "                    Wt[i] = den < max_w ? den : max_w;", "                    Wt[i] = den;"),
+    (CORE, "capped weight as the divisor", "                    F[i] = num / den;",
+     "                    F[i] = num / (den < max_w ? den : max_w);"),
+    (CORE, "behind-surface skip dropped", "                    if (eta < -mu) continue;", ""),
+    (CORE, "f not divided by mu", "                    float f = eta / mu;", "                    float f = eta;"),
+    (CORE, "no one-pixel image border", "    const float umax = (float)(W - 2), vmax = (float)(H - 2);",
+     "    const float umax = (float)(W - 1), vmax = (float)(H - 1);"),
+    (CORE, "segment ends at the surface", "    float z1 = d + mu;", "    float z1 = d;"),
+    (CORE, "pose inverse translation sign", "        for (int j = 0; j < 3; ++j) acc -= R[j][i] * t[j];",
+     "        for (int j = 0; j < 3; ++j) acc += R[j][i] * t[j];"),
+    (CORE, "no minimum raycast step",
+     "                if (step < ts) step = ts;\n                t = t + step;\n            }\n"
+     "            if (state != BEHIND_SURFACE) continue;\n            for (int r = 0; r < 2; ++r) {\n"
+     "                for (int i = 0; i < 3; ++i) q[i]",
+     "                t = t + step;\n            }\n"
+     "            if (state != BEHIND_SURFACE) continue;\n            for (int r = 0; r < 2; ++r) {\n"
+     "                for (int i = 0; i < 3; ++i) q[i]"),
+    (CORE, "trilinear x weights reversed", "    float c00 = lerpf(c000, c100, fr[0]);",
+     "    float c00 = lerpf(c100, c000, fr[0]);"),
+    (CORE, "trilinear z weights reversed", "    return lerpf(c0, c1, fr[2]);\n}\n\nenum",
+     "    return lerpf(c1, c0, fr[2]);\n}\n\nenum"),
     # learned confidence weight
     (CONF, "bf16 by truncation", "    u += 0x7fffu + lsb;\n    u &= 0xffff0000u;", "    u &= 0xffff0000u;"),
     (CONF, "bf16 ties away from zero", "    u += 0x7fffu + lsb;", "    u += 0x8000u; (void)lsb;"),

@@ -457,3 +457,50 @@ def test_raycast_of_empty_volume_misses_everywhere():
     sc = oracle.Scene(**w.params)
     vtx, nrm = sc.raycast(w.intr.width, w.intr.height, w.intr.as_array(), w.frame(0).T_wc)
     assert not vtx.any() and not nrm.any()
+
+
+def test_raycast_reproduces_a_linear_field():
+    """Trilinear interpolation reproduces a field that is linear in the voxel
+    coordinates, so over a volume holding the truncated distance of an
+    oblique plane (F = (n . (g s - P0)) / mu with every voxel read near the
+    crossing inside the band) the raycast's hits lie on the plane up to what
+    the march's last step and the two refinement steps leave, a bound known
+    per ray, and its normals equal n."""
+    s, mu = 0.01, 0.04
+    n = np.array([0.5, 0.3, -1.0])
+    n /= np.linalg.norm(n)
+    P0 = np.array([0.0, 0.0, 1.0])
+    sc = oracle.Scene(**scene_params(voxel_size=s, mu=mu))
+    l = np.arange(512)
+    local = np.stack([l % 8, (l // 8) % 8, l // 64], axis=1)
+    n_blocks = 0
+    for bx in range(-14, 14):
+        for by in range(-10, 10):
+            for bz in range(6, 26):
+                g = np.array([bx, by, bz]) * 8 + local
+                d = (g * float(np.float32(s)) - P0) @ n
+                if np.abs(d).min() > 0.12:
+                    continue
+                sc.set_block((bx, by, bz), np.clip(d / mu, -1.0, 1.0), 1.0)
+                n_blocks += 1
+    assert n_blocks > 500
+    intr = SMALL
+    vtx, nrm = sc.raycast(intr.width, intr.height, intr.as_array(), np.eye(4, dtype=np.float32))
+    hit = vtx[..., 3] > 0
+    assert hit.mean() > 0.99
+    X = vtx[..., :3][hit].astype(np.float64)
+    dist = (X - P0) @ n
+    # the march stops within s cos(theta) past the plane (its smallest step
+    # is s along the ray's depth unit), and each refinement step scales the
+    # distance by (1 - cos(theta)), theta between the ray and the normal
+    u, v = np.meshgrid(np.arange(intr.width), np.arange(intr.height))
+    ray = np.stack([(u - intr.cx) / intr.fx, (v - intr.cy) / intr.fy], -1)[hit]
+    c = np.abs(np.c_[ray, np.ones(len(ray))] @ n) / np.linalg.norm(np.c_[ray, np.ones(len(ray))], axis=1)
+    bound = s * c * (1.0 - c) ** 2
+    assert np.all(np.abs(dist) <= bound + 1e-3 * s), np.max(np.abs(dist) - bound)
+    assert np.median(np.abs(dist)) <= 0.02 * s
+    # the hit lies on the pixel's ray
+    np.testing.assert_allclose(X[:, :2] / X[:, 2:3], ray, atol=1e-5)
+    good = nrm[..., 3][hit] > 0
+    assert good.mean() > 0.99
+    np.testing.assert_allclose(nrm[..., :3][hit][good], np.broadcast_to(n, (good.sum(), 3)), atol=1e-4)
