@@ -68,6 +68,10 @@ MUTANTS = [
      "    float c00 = lerpf(c100, c000, fr[0]);"),
     (CORE, "trilinear z weights reversed", "    return lerpf(c0, c1, fr[2]);\n}\n\nenum",
      "    return lerpf(c1, c0, fr[2]);\n}\n\nenum"),
+    (CORE, "trilinear y weights reversed", "\n    float c0 = lerpf(c00, c10, fr[1]);",
+     "\n    float c0 = lerpf(c10, c00, fr[1]);"),
+    (CORE, "trilinear corners y and z swapped", "    float c010 = voxel_value(s, x, y + 1, z, &o[2])",
+     "    float c010 = voxel_value(s, x, y, z + 1, &o[2])"),
     # learned confidence weight
     (CONF, "bf16 by truncation", "    u += 0x7fffu + lsb;\n    u &= 0xffff0000u;", "    u &= 0xffff0000u;"),
     (CONF, "bf16 ties away from zero", "    u += 0x7fffu + lsb;", "    u += 0x8000u; (void)lsb;"),
