@@ -72,6 +72,17 @@ MUTANTS = [
      "\n    float c0 = lerpf(c10, c00, fr[1]);"),
     (CORE, "trilinear corners y and z swapped", "    float c010 = voxel_value(s, x, y + 1, z, &o[2])",
      "    float c010 = voxel_value(s, x, y, z + 1, &o[2])"),
+    (CORE, "sdf starts at 0", "        s->sdf[(size_t)ptr * ORC_BLOCK3 + i] = 1.0f;",
+     "        s->sdf[(size_t)ptr * ORC_BLOCK3 + i] = 0.0f;"),
+    (CORE, "coarse search without the step back",
+     "                        t = t - tB;\n                        state = SEARCH_BLOCK_FINE;\n                    }\n"
+     "                    continue;\n                }\n                if (!alloc) {\n"
+     "                    if (state == SEARCH_BLOCK_FINE) t = t + tmu;\n                    else state = SEARCH_BLOCK_COARSE;\n"
+     "                    continue;\n                }\n                int obs",
+     "                        state = SEARCH_BLOCK_FINE;\n                    }\n"
+     "                    continue;\n                }\n                if (!alloc) {\n"
+     "                    if (state == SEARCH_BLOCK_FINE) t = t + tmu;\n                    else state = SEARCH_BLOCK_COARSE;\n"
+     "                    continue;\n                }\n                int obs"),
     # learned confidence weight
     (CONF, "bf16 by truncation", "    u += 0x7fffu + lsb;\n    u &= 0xffff0000u;", "    u &= 0xffff0000u;"),
     (CONF, "bf16 ties away from zero", "    u += 0x7fffu + lsb;", "    u += 0x8000u; (void)lsb;"),
