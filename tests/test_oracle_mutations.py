@@ -145,6 +145,8 @@ MUTANTS = [
     (COLOUR, "extrinsic ignored", "    float Xc = row_apply(&cf->T[0], X, Y, Z);", "    float Xc = X; (void)row_apply;"),
     (COLOUR, "channels reversed", "        float p00 = (float)P[((size_t)v0 * cf->Wc + u0) * 3 + ch];",
      "        float p00 = (float)P[((size_t)v0 * cf->Wc + u0) * 3 + (2 - ch)];"),
+    (COLOUR, "unweighted colour mean", "        float nc = (wc * (float)c[ch] + obs) / (wc + 1.0f);",
+     "        float nc = ((float)c[ch] + obs) / 2.0f;"),
     (COLOUR, "colour weight steps by 2", "    float nw = wc + 1.0f;", "    float nw = wc + 2.0f;"),
     (COLOUR, "point colour from floor(q)", "            else g[a] = (int)floorf(q + 0.5f);",
      "            else g[a] = (int)floorf(q);"),    # combined map (Sec. 7.2), depth tracker (Sec. 4.1.1), Marching Cubes (Sec. 4)
@@ -177,6 +179,10 @@ MUTANTS = [
      "            const float res = -((dx * Np[0] + dy * Np[1]) + dz * Np[2]);"),
     (TRACK, "threshold on the distance, not its square", "            if (!(dist2 <= t2)) continue;",
      "            if (!(dist2 <= dist_thresh)) continue;"),
+    (TRACK, "Gauss-Newton right-hand side sign", "    for (int i = 0; i < 6; ++i) b[i] = -sums[21 + i];",
+     "    for (int i = 0; i < 6; ++i) b[i] = sums[21 + i];"),
+    (TRACK, "Cholesky divisor from the wrong row", "                L[i][j] = acc / L[j][j];",
+     "                L[i][j] = acc / L[i][i];"),
     (TRACK, "Rodrigues sine sign",
      "R[i][j] = (i == j ? 1.0 : 0.0) + a * K[i][j] + c * K2[i][j];",
      "R[i][j] = (i == j ? 1.0 : 0.0) - a * K[i][j] + c * K2[i][j];"),
