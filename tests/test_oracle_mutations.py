@@ -106,6 +106,9 @@ MUTANTS = [
     (CONF, "sign of the label term", "        loss += (o > 0 ? o : 0.0) - o * t + log1p(exp(-fabs(o)));",
      "        loss += (o > 0 ? o : 0.0) + o * t + log1p(exp(-fabs(o)));"),
     # swapping (Sec. 5)
+    (SWAP, "fusion weights crossed", "    float num = *W * *F + Wh * Fh;", "    float num = Wh * *F + *W * Fh;"),
+    (SWAP, "host value replaces the fused one", "    *F = num / den;\n    *W = den < max_w",
+     "    *F = Fh; (void)num;\n    *W = den < max_w"),
     (SWAP, "no weight clamp", "    *W = den < max_w ? den : max_w;", "    *W = den;"),
     (SWAP, "host weight 0 not skipped", "    if (!(Wh > 0.0f)) return;\n    if (!(*W > 0.0f)) {",
      "    if (!(*W > 0.0f) && (Wh > 0.0f)) {"),
