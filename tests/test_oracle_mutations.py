@@ -164,6 +164,13 @@ MUTANTS = [
     (COMB, "allocation test on the first submap only",
      "    for (int i = 0; i < n; ++i) {\n        float q[3];\n        if (!submap_coords(P + 16 * i, X, inv_s, q)) continue;\n        int bx",
      "    for (int i = 0; i < 1 && i < n; ++i) {\n        float q[3];\n        if (!submap_coords(P + 16 * i, X, inv_s, q)) continue;\n        int bx"),
+    (COMB, "corner bits y and z swapped",
+     "        int gx = x + (k & 1), gy = y + ((k >> 1) & 1), gz = z + ((k >> 2) & 1);",
+     "        int gx = x + (k & 1), gy = y + ((k >> 2) & 1), gz = z + ((k >> 1) & 1);"),
+    (COMB, "x weights reversed", "        float c00 = lerpf(v[m][0], v[m][1], fr[0]);",
+     "        float c00 = lerpf(v[m][1], v[m][0], fr[0]);"),
+    (COMB, "unallocated voxel value 0", "            c[k] = 1.0f;\n            w[k] = 0.0f;",
+     "            c[k] = 0.0f;\n            w[k] = 0.0f;"),
     (COMB, "default 0 where unobserved", "    return dsum > 0.0f ? num / dsum : 1.0f;", "    return dsum > 0.0f ? num / dsum : 0.0f;"),
     (TRACK, "cross product order in the Jacobian",
      "            const float J[6] = {pw[1] * Np[2] - pw[2] * Np[1], pw[2] * Np[0] - pw[0] * Np[2],\n"
