@@ -238,6 +238,31 @@ def make_params(voxel_size, mu, max_w, num_buckets, num_excess, num_blocks, z_mi
                             int(num_blocks), float(z_min), float(z_max), int(weight_mode))
 
 
+CONFIG_DIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "configs")
+
+
+def load_config(name_or_path):
+    """A scene configuration from JSON: {"scene": the itm_scene_params fields,
+    "intrinsics": the itm_intrinsics fields, ...}.  name_or_path is one of
+    the files in configs/ by name ("tiny", "kinect", "large") or a path.
+    Returns (a dict of scene parameters for Scene(**params), itm_intrinsics).
+    Unknown or missing fields raise ValueError."""
+    import json
+    path = name_or_path
+    if not os.path.exists(path):
+        path = os.path.join(CONFIG_DIR, "%s.json" % name_or_path)
+    with open(path) as f:
+        cfg = json.load(f)
+    scene, intr = dict(cfg.get("scene", {})), dict(cfg.get("intrinsics", {}))
+    want_s = {n for n, _ in itm_scene_params._fields_}
+    want_i = {n for n, _ in itm_intrinsics._fields_}
+    scene.setdefault("weight_mode", 0)
+    if set(scene) != want_s or set(intr) != want_i:
+        raise ValueError("%s: scene fields %s and intrinsics fields %s expected" % (path, sorted(want_s),
+                                                                                    sorted(want_i)))
+    return scene, make_intrinsics(**intr)
+
+
 def _check(code, what):
     if code != ITM_OK:
         raise ItmError(code, what)
@@ -596,6 +621,12 @@ class Scene:
                            num_excess=num_excess, num_blocks=num_blocks, z_min=z_min, z_max=z_max,
                            weight_mode=weight_mode)
         self.handle = itm_scene_create(make_params(**self.params))
+
+    @classmethod
+    def from_config(cls, name_or_path):
+        """(Scene, itm_intrinsics) of a JSON configuration (load_config)."""
+        params, intr = load_config(name_or_path)
+        return cls(**params), intr
 
     def close(self):
         if getattr(self, "handle", None):
