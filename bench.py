@@ -257,6 +257,15 @@ def sum_over_ranks(value, world, device=None):
 
 # ----------------------------------------------------------------- CPU oracle
 
+def write_frames_jsonl(path, frames, stage):
+    """One JSON line per timed frame: its index and the device time of each
+    stage (ms), for plots of the per-frame cost along the trajectory."""
+    names = ("u16_to_f32_and_allocate_ms", "integrate_ms", "raycast_ms")
+    with open(path, "w") as f:
+        for k, row in zip(frames, stage):
+            f.write(json.dumps(dict({"frame": int(k)}, **{n: float(v) for n, v in zip(names, row)})) + "\n")
+
+
 def host_cpu():
     """CPU model and logical core count of this host, for the CPU baseline."""
     import platform
@@ -852,6 +861,8 @@ def run_ours(args, world, rank, local):
     if st1["status"] != 0:
         raise RuntimeError("device status %#x during the timed region" % st1["status"])
     stage = np.array([[ev[i][j].elapsed_time(ev[i][j + 1]) for j in range(3)] for i in range(args.steps)])
+    if args.frames_jsonl and rank == 0:
+        write_frames_jsonl(args.frames_jsonl, [(args.warmup + i) % n_frames for i in range(args.steps)], stage)
     step_ms = stage.sum(axis=1)
     total_ms = float(step_ms.sum())
     total_ms_max = max_over_ranks(total_ms, world, dev)
@@ -1051,6 +1062,8 @@ def main(argv=None):
     ap.add_argument("--no-swap", dest="swap", action="store_false")
     ap.add_argument("--no-colour", dest="colour", action="store_false",
                     help="skip the colour-voxel section (Sec. 3.1) on the room trajectory")
+    ap.add_argument("--frames-jsonl", metavar="PATH",
+                    help="also write each timed frame's stage times to PATH, one JSON line per frame")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="kinect",
                     help="configuration of the per-frame loop (default: the 640x480 / 5 mm room the metric is "
                          "quoted on); the batched, learned, tracking, mesh and swapping sections run with the default only")

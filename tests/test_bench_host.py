@@ -36,3 +36,14 @@ def test_peak_from_the_measured_file_else_the_fallback(tmp_path, monkeypatch):
 def test_job_throughput_counts_all_ranks_over_the_slowest():
     assert bench.job_throughput(290, 1, 58.0) == 290 / 0.058
     assert bench.job_throughput(290, 4, 60.0) == 4 * 290 / 0.060
+
+
+def test_frames_jsonl(tmp_path):
+    import json
+    import numpy as np
+    import bench
+    p = tmp_path / "f.jsonl"
+    bench.write_frames_jsonl(str(p), [10, 11], np.array([[0.05, 0.03, 0.1], [0.06, 0.02, 0.2]]))
+    rows = [json.loads(l) for l in p.read_text().splitlines()]
+    assert rows == [{"frame": 10, "u16_to_f32_and_allocate_ms": 0.05, "integrate_ms": 0.03, "raycast_ms": 0.1},
+                    {"frame": 11, "u16_to_f32_and_allocate_ms": 0.06, "integrate_ms": 0.02, "raycast_ms": 0.2}]
