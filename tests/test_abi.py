@@ -171,3 +171,28 @@ def test_scene_parameters_checked_on_the_host():
         p = itm.itm_scene_params(**dict(base, weight_mode=1, max_w=1000))
         out = ctypes.c_void_p()
         assert itm._lib.itm_scene_create(ctypes.byref(p), ctypes.byref(out)) == itm.ITM_ERR_CUDA
+
+
+def test_host_hash_on_a_million_triples():
+    """The library's hash (the same __host__ __device__ function the kernels
+    call) on 10^6 random int16 triples, extremes and negatives included,
+    equals the printed function of Sec. 3.2 evaluated with numpy's uint32
+    wrap-around from the golden primes, and the oracle's."""
+    import oracle
+    import paper_1708_00783_gb300 as itm
+    from tests.test_oracle_pins import golden
+    g = golden("hash_function.txt")
+    rng = np.random.default_rng(3)
+    xyz = rng.integers(-32768, 32768, size=(10 ** 6, 3))
+    xyz[:8] = [[-32768, -32768, -32768], [32767, 32767, 32767], [-1, 0, 1], [0, 0, 0],
+               [-32768, 32767, 0], [1, -1, -32768], [32767, -32768, -1], [-2, -3, -4]]
+    for nb in (1 << 10, 1 << 20):
+        p = np.array([g["prime_x"], g["prime_y"], g["prime_z"]], dtype=np.uint64)
+        u = (xyz.astype(np.int64) & 0xFFFFFFFF).astype(np.uint64)
+        h = ((u * p) & 0xFFFFFFFF)
+        want = ((h[:, 0] ^ h[:, 1] ^ h[:, 2]) & (nb - 1)).astype(np.int64)
+        f = itm._lib.itm_hash_index
+        got = np.fromiter((f(int(x), int(y), int(z), nb) for x, y, z in xyz), dtype=np.int64, count=len(xyz))
+        assert np.array_equal(got, want)
+        sample = xyz[:2000]
+        assert all(oracle.hash_index(x, y, z, nb) == want[i] for i, (x, y, z) in enumerate(sample))
