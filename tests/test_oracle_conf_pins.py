@@ -109,6 +109,33 @@ def test_forward_of_constructed_networks():
     assert o == pytest.approx(6.0 * (1.0 + 2.0 ** -9) + 0.7)
 
 
+def test_forward_rounds_each_product_input_to_bfloat16():
+    """Both products take bfloat16 inputs (as the tensor cores do): the
+    features before layer 1 and the layer-1 activations before layer 2.
+    Each case is built so that only one of the two roundings decides it."""
+    P = _zeros()
+    W1, b1, W2, b2, w3, b3 = _views(P)
+    # features: x = 1 + 2^-8 is a tie and rounds to 1; with the weight 1.5
+    # the activation 1.5 is exact, while 1.5 (1 + 2^-8) would round up to
+    # 1.5 + 2^-7 before layer 2
+    W1[0, 10], W2[0, 0], w3[0] = 1.5, 1.0, 1.0
+    x = np.zeros(52)
+    x[10] = 1.0 + 2.0 ** -8
+    o, h1, _ = oracle.mlp_forward(P, x, round_bf16=True)
+    assert o == 1.5 and h1[0] == 1.5
+    # layer-1 activation: an exact feature plus the float bias 2^-9 gives
+    # 1 + 2^-9, which rounds to 1 before layer 2
+    P = _zeros()
+    W1, b1, W2, b2, w3, b3 = _views(P)
+    W1[1, 11], b1[1], W2[2, 1], w3[2] = 1.0, 2.0 ** -9, 1.0, 1.0
+    x = np.zeros(52)
+    x[11] = 1.0
+    o, h1, h2 = oracle.mlp_forward(P, x, round_bf16=True)
+    assert h1[1] == 1.0 + 2.0 ** -9 and h2[2] == 1.0 and o == 1.0
+    o, _, _ = oracle.mlp_forward(P, x, round_bf16=False)
+    assert o == 1.0 + 2.0 ** -9
+
+
 def test_forward_uses_both_hidden_biases():
     P = _zeros()
     W1, b1, W2, b2, w3, b3 = _views(P)

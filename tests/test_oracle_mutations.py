@@ -93,6 +93,15 @@ MUTANTS = [
     (CONF, "normal cross product order",
      "        double n[3] = {a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]};",
      "        double n[3] = {b[1] * a[2] - b[2] * a[1], b[2] * a[0] - b[0] * a[2], b[0] * a[1] - b[1] * a[0]};"),
+    (CONF, "W1 read with the wrong stride",
+     "        for (int k = 0; k < ORC_NF; ++k) acc += maybe_bf16(W1[m * ORC_NF + k], round_bf16) * xin[k];",
+     "        for (int k = 0; k < ORC_NF; ++k) acc += maybe_bf16(W1[k * ORC_NH + m], round_bf16) * xin[k];"),
+    (CONF, "b1 dropped", "        a1[m] = relu(acc + b1[m]);", "        a1[m] = relu(acc);"),
+    (CONF, "features not rounded to bfloat16",
+     "    for (int k = 0; k < ORC_NF; ++k) xin[k] = maybe_bf16(x[k], round_bf16);",
+     "    for (int k = 0; k < ORC_NF; ++k) xin[k] = x[k];"),
+    (CONF, "layer-2 input not rounded to bfloat16", "        a1in[m] = maybe_bf16(a1[m], round_bf16);",
+     "        a1in[m] = a1[m];"),
     (CONF, "no ReLU on layer 2", "        a2[n] = relu(acc + b2[n]);", "        a2[n] = acc + b2[n];"),
     (CONF, "b2 dropped", "        a2[n] = relu(acc + b2[n]);", "        a2[n] = relu(acc);"),
     (CONF, "b3 dropped", "    double o = b3[0];", "    double o = 0.0; (void)b3;"),
