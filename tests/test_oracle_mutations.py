@@ -216,6 +216,11 @@ MUTANTS = [
     (MESH, "a face walked clockwise", "    {0, 4, 6, 2}, {1, 3, 7, 5},", "    {0, 2, 6, 4}, {1, 3, 7, 5},"),
     (MESH, "F = 0 taken as inside", "            int ia = F[a] < 0.0f, ib = F[b] < 0.0f;",
      "            int ia = F[a] <= 0.0f, ib = F[b] <= 0.0f;"),
+    (MESH, "corner z offset from the y bit",
+     "                ok = observed_value(s, g[0] + (k & 1), g[1] + ((k >> 1) & 1), g[2] + (k >> 2), &F[k]);",
+     "                ok = observed_value(s, g[0] + (k & 1), g[1] + ((k >> 1) & 1), g[2] + ((k >> 1) & 1), &F[k]);"),
+    (MESH, "edge axes x and y swapped", "                    int axis = (c - a) == 1 ? 0 : (c - a) == 2 ? 1 : 2;",
+     "                    int axis = (c - a) == 2 ? 0 : (c - a) == 1 ? 1 : 2;"),
     (MESH, "corner offset on the wrong axis", "                        float coord = (float)(g[k] + ((a >> k) & 1));",
      "                        float coord = (float)(g[k] + ((a >> ((k + 1) % 3)) & 1));"),
 ]
