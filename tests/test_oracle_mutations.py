@@ -191,6 +191,10 @@ MUTANTS = [
     (TRACK, "association without rounding",
      "            const size_t o = 4 * ((size_t)(int)(vr + 0.5f) * Wr + (int)(ur + 0.5f));",
      "            const size_t o = 4 * ((size_t)(int)(vr) * Wr + (int)(ur));"),
+    (TRACK, "association through the live pose", "    float M[16];\n    rigid_inverse(T_ref, M);\n    const float t2",
+     "    float M[16];\n    rigid_inverse(T_g, M);\n    const float t2"),
+    (TRACK, "normal validity not checked", "            if (!(Vp[3] > 0.0f && Np[3] > 0.0f)) continue;",
+     "            if (!(Vp[3] > 0.0f)) continue;"),
     (TRACK, "invalid depths in the pyramid mean", "                if (d > 0.0f) {\n                    sum = sum + d;",
      "                if (1) {\n                    sum = sum + d;"),
     (TRACK, "pyramid centre c/2", "    out[2] = (in[2] - 0.5f) / 2.0f;", "    out[2] = in[2] / 2.0f;"),

@@ -134,6 +134,27 @@ def test_plane_offset_closed_form():
     assert not ok and np.array_equal(T2, Tg)
 
 
+def test_pixels_without_a_vertex_or_normal_are_not_used():
+    """The reduction uses a reference pixel only when both its vertex and its
+    normal are valid (w > 0): on the offset plane, pixels whose normal (or
+    vertex) is marked invalid drop out of the count and of every sum."""
+    intr, V, N, D = _plane_setup()
+    delta = 0.01
+    Tg = np.eye(4, dtype=np.float32)
+    Tg[2, 3] = delta
+    full, _ = oracle.icp_reduce(D, intr.as_array(), Tg, V, N, intr.as_array(), np.eye(4), 0.05)
+    N2, V2 = N.copy(), V.copy()
+    N2[:, ::2, 3] = 0.0          # every other column has no normal
+    V2[::3, :, 3] = 0.0          # every third row has no vertex
+    s, _ = oracle.icp_reduce(D, intr.as_array(), Tg, V2, N2, intr.as_array(), np.eye(4), 0.05)
+    used = (N2[..., 3] > 0) & (V2[..., 3] > 0)
+    n = int(used.sum())
+    assert 0 < n < D.size and s[28] == n
+    assert s[27] == pytest.approx(n * delta ** 2, rel=1e-5)
+    assert s[20] == n and s[21 + 5] == pytest.approx(n * delta, rel=1e-5)
+    assert full[28] == D.size
+
+
 def _box_view():
     scene = AnalyticScene([RoomInside((-1.0, 0.0, -1.5), (1.5, 2.0, 1.0))])
     intr = Intrinsics(64, 48, 50.0, 50.0, 31.5, 23.5)
