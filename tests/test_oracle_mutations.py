@@ -118,6 +118,9 @@ MUTANTS = [
     (SWAP, "fusion weights crossed", "    float num = *W * *F + Wh * Fh;", "    float num = Wh * *F + *W * Fh;"),
     (SWAP, "host value replaces the fused one", "    *F = num / den;\n    *W = den < max_w",
      "    *F = Fh; (void)num;\n    *W = den < max_w"),
+    (SWAP, "a block waiting for its host data swapped out",
+     "    return e->ptr >= 0 && s->swap_state[idx] == ORC_SW_DEVICE && s->frame - s->touch[idx] >= s->swap_idle;",
+     "    return e->ptr >= 0 && s->frame - s->touch[idx] >= s->swap_idle;"),
     (SWAP, "no weight clamp", "    *W = den < max_w ? den : max_w;", "    *W = den;"),
     (SWAP, "host weight 0 not skipped", "    if (!(Wh > 0.0f)) return;\n    if (!(*W > 0.0f)) {",
      "    if (!(*W > 0.0f) && (Wh > 0.0f)) {"),
@@ -160,6 +163,9 @@ MUTANTS = [
     (COLOUR, "unweighted colour mean", "        float nc = (wc * (float)c[ch] + obs) / (wc + 1.0f);",
      "        float nc = ((float)c[ch] + obs) / 2.0f;"),
     (COLOUR, "colour weight steps by 2", "    float nw = wc + 1.0f;", "    float nw = wc + 2.0f;"),
+    (COLOUR, "point colour with y and z strides swapped",
+     "        memcpy(o, &s->rgbw[((size_t)ptr * ORC_BLOCK3 + (g[0] & 7) + 8 * (g[1] & 7) + 64 * (g[2] & 7)) * 4], 4);",
+     "        memcpy(o, &s->rgbw[((size_t)ptr * ORC_BLOCK3 + (g[0] & 7) + 64 * (g[1] & 7) + 8 * (g[2] & 7)) * 4], 4);"),
     (COLOUR, "point colour from floor(q)", "            else g[a] = (int)floorf(q + 0.5f);",
      "            else g[a] = (int)floorf(q);"),    # combined map (Sec. 7.2), depth tracker (Sec. 4.1.1), Marching Cubes (Sec. 4)
     (COMB, "combined sum not normalised", "    return dsum > 0.0f ? num / dsum : 1.0f;", "    return dsum > 0.0f ? num : 1.0f;"),

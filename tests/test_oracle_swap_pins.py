@@ -81,6 +81,27 @@ def test_fusion_closed_forms():
     assert sc.swap_counters() == dict(host_data=0, swapped_out=0, waiting=0, moved_in=1, moved_out=1)
 
 
+def test_block_waiting_for_its_host_data_stays_on_the_device():
+    """A block met again while its host data waits for the secondary fusion
+    is no swap-out candidate, however idle (its device copy would overwrite
+    the waiting data): swap_out moves nothing until swap_in has fused it, and
+    the fusion then gives the closed-form mean of both."""
+    sc = oracle.Scene(**scene_params())
+    b = (1, 2, 3)
+    sc.set_block(b, np.full(512, -0.25, np.float32), np.full(512, 3.0, np.float32))
+    sc.swap_enable(64, idle_frames=0)
+    assert sc.swap_out() == 1
+    sc.set_block(b, np.full(512, 0.5, np.float32), np.full(512, 1.0, np.float32))
+    assert sc.swap_counters()["waiting"] == 1
+    assert sc.swap_out() == 0
+    assert sc.swap_counters()["waiting"] == 1
+    assert sc.swap_in() == 1
+    c, F, W = sc.export()
+    assert _keys(c) == {b}
+    assert np.all(F[0] == -0.0625) and np.all(W[0] == 4)   # (1 * 0.5 + 3 * -0.25) / 4
+    assert sc.swap_out() == 1                              # fused: a candidate again
+
+
 def test_round_trip_restores_the_block():
     """Out to the host, met again, fused into an empty device block: the
     block comes back bit for bit (every device weight is 0)."""
