@@ -55,6 +55,9 @@ MUTANTS = [
     (CORE, "no one-pixel image border", "    const float umax = (float)(W - 2), vmax = (float)(H - 2);",
      "    const float umax = (float)(W - 1), vmax = (float)(H - 1);"),
     (CORE, "segment ends at the surface", "    float z1 = d + mu;", "    float z1 = d;"),
+    (CORE, "segment starts at the surface", "    float z0 = d - mu;", "    float z0 = d;"),
+    (CORE, "near end not clamped in front of the camera", "    if (z0 < 1e-3f) z0 = 1e-3f;", ""),
+    (CORE, "depth range ignored in allocation", "    if (d < s->z_min || d > s->z_max) return 0;", ""),
     (CORE, "pose inverse translation sign", "        for (int j = 0; j < 3; ++j) acc -= R[j][i] * t[j];",
      "        for (int j = 0; j < 3; ++j) acc += R[j][i] * t[j];"),
     (CORE, "no minimum raycast step",

@@ -259,6 +259,25 @@ def test_allocation_equals_brute_force_sweep(seed):
     assert sc.num_allocated == len(got)
 
 
+def test_allocation_near_the_camera_starts_in_front_of_it():
+    """Depths closer than mu: the segment's near end is clamped to 1 mm in
+    front of the camera (a segment starting behind it would allocate blocks
+    there); the allocated set still equals the brute-force sweep."""
+    rng = np.random.default_rng(7)
+    intr = Intrinsics(12, 9, 10.0, 10.0, 5.5, 4.0)
+    T = random_pose(rng)
+    depth = rng.uniform(0.02, 0.3, size=(9, 12)).astype(np.float32)
+    p = scene_params(mu=0.2, z_min=0.01, z_max=2.9)
+    assert (depth < p["mu"]).mean() > 0.5
+    sc = oracle.Scene(**p)
+    assert sc.allocate(depth, intr.as_array(), T) == 0
+    got = {tuple(int(x) for x in c) for c in sc.export(with_voxels=False)[0]}
+    sure, maybe = brute_force_blocks(depth, intr, T, p["voxel_size"], p["mu"], p["z_min"], p["z_max"], eps=1e-4)
+    assert len(sure) > 50
+    assert sure <= got, sorted(sure - got)[:5]
+    assert got <= maybe, sorted(got - maybe)[:5]
+
+
 def test_hash_function_matches_printed_constants():
     """Sec. 3.2: hashIndex xors the coordinates times the three printed primes
     (unsigned 32-bit wrap-around) and masks with buckets - 1."""
