@@ -60,6 +60,9 @@ MUTANTS = [
     (CORE, "depth range ignored in allocation", "    if (d < s->z_min || d > s->z_max) return 0;", ""),
     (CORE, "pose inverse translation sign", "        for (int j = 0; j < 3; ++j) acc -= R[j][i] * t[j];",
      "        for (int j = 0; j < 3; ++j) acc += R[j][i] * t[j];"),
+    (CORE, "voxels behind the camera not skipped", "                    if (Z <= 0.0f) continue;\n                    float u",
+     "                    float u"),
+    (CORE, "raycast starts at 0, not z_min", "            float t = s->z_min;", "            float t = 0.0f;"),
     (CORE, "no minimum raycast step",
      "                if (step < ts) step = ts;\n                t = t + step;\n            }\n"
      "            if (state != BEHIND_SURFACE) continue;\n            for (int r = 0; r < 2; ++r) {\n"

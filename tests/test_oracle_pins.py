@@ -523,3 +523,28 @@ def test_raycast_reproduces_a_linear_field():
     good = nrm[..., 3][hit] > 0
     assert good.mean() > 0.99
     np.testing.assert_allclose(nrm[..., :3][hit][good], np.broadcast_to(n, (good.sum(), 3)), atol=1e-4)
+
+
+def test_raycast_starts_at_z_min():
+    """The march covers depths z_min .. z_max only: a plane at 0.5 m is hit
+    with z_min = 0.1 and not reported with z_min = 0.8 (the ray starts beyond
+    it, in empty space)."""
+    s, mu = 0.01, 0.04
+    l = np.arange(512)
+    local = np.stack([l % 8, (l // 8) % 8, l // 64], axis=1)
+    for z_min, want_hits in ((0.1, True), (0.8, False)):
+        sc = oracle.Scene(**scene_params(voxel_size=s, mu=mu, z_min=z_min, z_max=3.0))
+        for bx in range(-6, 6):
+            for by in range(-5, 5):
+                for bz in range(4, 9):
+                    g = np.array([bx, by, bz]) * 8 + local
+                    d = 0.5 - g[:, 2] * float(np.float32(s))
+                    if np.abs(d).min() > 0.12:
+                        continue
+                    sc.set_block((bx, by, bz), np.clip(d / mu, -1.0, 1.0), 1.0)
+        vtx, _ = sc.raycast(SMALL.width, SMALL.height, SMALL.as_array(), np.eye(4, dtype=np.float32))
+        hit = vtx[..., 3] > 0
+        if want_hits:
+            assert hit.mean() > 0.9 and np.allclose(vtx[..., 2][hit], 0.5, atol=0.2 * s)
+        else:
+            assert not hit.any()
