@@ -2,7 +2,8 @@
 
 Each case copies oracle/ with one source line changed, plus tests/ and synth/,
 into a temporary directory and runs there the pin module for that part of the
-oracle; the module must fail, on an assertion (not on a build error).  This is
+oracle; the module must fail, on an assertion (not on a build error).  The
+cases run side by side, one subprocess each.  This is
 what ties the pins to something other than the oracle itself: a plausible
 slip in an operation, an index, an order, a sign or a bound breaks at least
 one of them.  The mistakes are planted in the oracle only, on the CPU.
@@ -13,7 +14,6 @@ import shutil
 import subprocess
 import sys
 
-import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -242,19 +242,37 @@ MUTANTS = [
 ]
 
 
-@pytest.mark.parametrize("module,mistake,old,new", MUTANTS, ids=[m[1] for m in MUTANTS])
-def test_planted_mistake_fails_a_pin(tmp_path, module, mistake, old, new):
+def _run_mutant(root, module, mistake, old, new):
+    """Plant one mistake in a copy of the oracle under root and run its pin
+    module there; returns why the pins did not catch it, or None."""
     src = open(os.path.join(ROOT, "oracle", "itm_oracle.c")).read()
-    assert src.count(old) == 1, "the planted line no longer matches the oracle once: " + mistake
+    if src.count(old) != 1:
+        return "the planted line no longer matches the oracle once"
     for d in ("tests", "synth"):
-        shutil.copytree(os.path.join(ROOT, d), tmp_path / d, ignore=shutil.ignore_patterns("__pycache__"))
-    (tmp_path / "oracle").mkdir()
-    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), tmp_path / "oracle" / "__init__.py")
-    (tmp_path / "oracle" / "itm_oracle.c").write_text(src.replace(old, new))
+        shutil.copytree(os.path.join(ROOT, d), os.path.join(root, d), ignore=shutil.ignore_patterns("__pycache__"))
+    os.mkdir(os.path.join(root, "oracle"))
+    shutil.copy(os.path.join(ROOT, "oracle", "__init__.py"), os.path.join(root, "oracle", "__init__.py"))
+    with open(os.path.join(root, "oracle", "itm_oracle.c"), "w") as f:
+        f.write(src.replace(old, new))
     # the pin modules need no GPU check (and so no torch import) in the copy
-    (tmp_path / "tests" / "conftest.py").write_text(
-        "import os, sys\nsys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))\n")
+    with open(os.path.join(root, "tests", "conftest.py"), "w") as f:
+        f.write("import os, sys\nsys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))\n")
     r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider", "tests/" + module],
-                       cwd=tmp_path, capture_output=True, text=True, timeout=900)
-    assert r.returncode != 0, "the pins did not catch: " + mistake
-    assert "assert" in r.stdout, "failed for another reason than an assertion:\n" + r.stdout[-2000:]
+                       cwd=root, capture_output=True, text=True, timeout=900)
+    if r.returncode == 0:
+        return "the pins did not catch it"
+    if "assert" not in r.stdout:
+        return "failed for another reason than an assertion:\n" + r.stdout[-1500:]
+    return None
+
+
+def test_every_planted_mistake_fails_a_pin(tmp_path):
+    """Each mistake in its own copy, the copies run side by side on the host's
+    cores (they share nothing)."""
+    from concurrent.futures import ThreadPoolExecutor
+    assert len({m[1] for m in MUTANTS}) == len(MUTANTS)
+    workers = max(1, min(len(MUTANTS), os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as pool:
+        futs = [pool.submit(_run_mutant, str(tmp_path / ("m%03d" % i)), *m) for i, m in enumerate(MUTANTS)]
+        escaped = [(m[0], m[1], f.result()) for m, f in zip(MUTANTS, futs) if f.result() is not None]
+    assert not escaped, escaped
