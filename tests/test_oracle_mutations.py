@@ -63,6 +63,9 @@ MUTANTS = [
     (CORE, "voxels behind the camera not skipped", "                    if (Z <= 0.0f) continue;\n                    float u",
      "                    float u"),
     (CORE, "raycast starts at 0, not z_min", "            float t = s->z_min;", "            float t = 0.0f;"),
+    (CORE, "normal where a sampled voxel is unobserved",
+     "                float fm = trilinear(s, qm, &obs);\n                g[a] = fp - fm;\n            }\n            float gl = sqrtf((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);\n            if (obs && gl > 0.0f) {",
+     "                float fm = trilinear(s, qm, &obs);\n                g[a] = fp - fm;\n            }\n            float gl = sqrtf((g[0] * g[0] + g[1] * g[1]) + g[2] * g[2]);\n            if (gl > 0.0f) {"),
     (CORE, "no minimum raycast step",
      "                if (step < ts) step = ts;\n                t = t + step;\n            }\n"
      "            if (state != BEHIND_SURFACE) continue;\n            for (int r = 0; r < 2; ++r) {\n"
