@@ -143,9 +143,12 @@ __global__ void __launch_bounds__(256) batch_visible_kernel(const ItemDev *__res
     }
 }
 
-__global__ void __launch_bounds__(64) batch_integrate_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
+__global__ void __launch_bounds__(64) batch_integrate_kernel(const ItemDev *__restrict__ items, const BatchHead *head,
+                                                             float2 nz)
 {
     __shared__ int prefix[kMaxItems + 1];
+    __shared__ float2 rcp_w[256];
+    fill_rcp_w(rcp_w);  // read after cta_prefix's barrier
     const int n = head->n;
     const int total = cta_prefix(items, n, prefix, [](const ItemDev &it) {
         return min(__ldcg(&it.s.ctr->n_visible), it.s.nv);
@@ -164,7 +167,7 @@ __global__ void __launch_bounds__(64) batch_integrate_kernel(const ItemDev *__re
         const short4 b = __ldg(&it.s.block_pos[ptr]);
         unsigned updated = 0;
         short4 unused = b;
-        integrate_block<0>(it.s, it.depth, nullptr, it.in, it.M, ptr, b, t, updated, false, 0, unused);
+        integrate_block<0>(it.s, it.depth, nullptr, it.in, it.M, ptr, b, t, updated, false, 0, unused, rcp_w, nz);
         for (int o = 16; o > 0; o >>= 1) updated += __shfl_xor_sync(kFull, updated, o);
         if ((t & 31) == 0 && updated) atomicAdd(&it.s.ctr->updated, (unsigned long long)updated);
     }
@@ -278,7 +281,7 @@ static cudaError_t launch_stages(itm_batch *b, cudaStream_t st)
     batch_commit_kernel<<<b->grid[ST_COMMIT], 256, 0, st>>>(it, h);
     batch_overflow_kernel<<<b->max_items, kOvfThreads, 0, st>>>(it, h);
     batch_visible_kernel<<<b->grid[ST_VISIBLE], 256, 0, st>>>(it, h);
-    batch_integrate_kernel<<<b->grid[ST_INTEGRATE], 64, 0, st>>>(it, h);
+    batch_integrate_kernel<<<b->grid[ST_INTEGRATE], 64, 0, st>>>(it, h, make_float2(-0.0f, -0.0f));
     batch_range_kernel<<<b->grid[ST_RANGE], 256, 0, st>>>(it, h);
     batch_raycast_kernel<<<b->grid[ST_RAYCAST], 256, 0, st>>>(it, h);
     return cudaGetLastError();

@@ -9,18 +9,19 @@
 // processed.
 //
 // Each voxel runs the listing computeUpdatedVoxelDepthInfo with IEEE
-// round-to-nearest operations in the listing's order (no fused multiply-add,
-// correctly rounded divisions), so the skip decisions, the pixel read, the
-// weights and the sdf values are reproducible bit for bit.  The thread first
-// projects its eight voxels (no memory access), then issues their eight depth
-// reads together, then takes the update decisions: the reads overlap instead
-// of waiting on each other.  (Evaluating the projection with an approximate
-// reciprocal plus an exact fallback near decision boundaries measured no
-// faster: the kernel is bound by instruction issue across the whole voxel
-// update, not by the divisions.  The packed f32x2 add/multiply of sm_100+ was
-// also tried: in this broadcast-operand chain it did not reproduce the
-// separately rounded scalar results.)  Small integers move between int and
-// float through the 2^23 mantissa trick (exact for 0 <= n < 2^23) instead of
+// round-to-nearest results in the listing's order (no product fused into a
+// sum), so the skip decisions, the pixel read, the weights and the sdf values
+// are reproducible bit for bit.  The thread first projects its eight voxels
+// (no memory access), then issues their eight depth reads together, then
+// takes the update decisions: the reads overlap instead of waiting on each
+// other.  The kernel is bound by instruction issue, so the arithmetic runs on
+// voxel pairs with the packed FP32x2 add / multiply / FMA of sm_100+, and
+// each of the four quotients per voxel (u, v, eta / mu, the running mean) is
+// the correctly rounded quotient from a correctly rounded reciprocal plus
+// FMA residual corrections (Markstein 1990) instead of an IEEE division: one
+// reciprocal of Z serves both pixel coordinates, 1 / mu is computed once per
+// scene and 1 / (W + 1) comes from a 256-entry table in shared memory.  The
+// pixel index is truncated by a round-toward-zero add of 2^23 instead of
 // conversion instructions.
 //
 // The decision needs no voxel data: a thread loads a 16-byte quad of sdf
@@ -37,8 +38,14 @@ constexpr int kThreads = 64;
 
 template <int MODE>  // 0: constant weight 1, uint8 weights; 1: per-pixel weight, float weights
 __global__ void __launch_bounds__(kThreads) integrate_kernel(SceneDev s, const float *__restrict__ depth,
-                                                             const float *__restrict__ wpx, Intr in, Mat34 M)
+                                                             const float *__restrict__ wpx, Intr in, Mat34 M,
+                                                             float2 nz)
 {
+    __shared__ float2 rcp_w[256];
+    if (MODE == 0) {
+        fill_rcp_w(rcp_w);
+        __syncthreads();
+    }
     const int n = min(__ldcg(&s.ctr->n_visible), s.nv);
     const int t = threadIdx.x;
     unsigned updated = 0;
@@ -55,7 +62,7 @@ __global__ void __launch_bounds__(kThreads) integrate_kernel(SceneDev s, const f
         int ptr_next = 0;
         if (i_next < n) ptr_next = __ldg(&s.visible[i_next]);
         short4 b_next = b;
-        integrate_block<MODE>(s, depth, wpx, in, M, ptr, b, t, updated, i_next < n, ptr_next, b_next);
+        integrate_block<MODE>(s, depth, wpx, in, M, ptr, b, t, updated, i_next < n, ptr_next, b_next, rcp_w, nz);
         i = i_next;
         ptr = ptr_next;
         b = b_next;
@@ -89,8 +96,9 @@ int integrate_grid()
 cudaError_t launch_integrate(const SceneDev &s, const float *depth, const float *wpx, const Intr &in,
                              const Mat34 &M_d, cudaStream_t st)
 {
-    if (wpx) integrate_kernel<1><<<integrate_grid<1>(), kThreads, 0, st>>>(s, depth, wpx, in, M_d);
-    else integrate_kernel<0><<<integrate_grid<0>(), kThreads, 0, st>>>(s, depth, nullptr, in, M_d);
+    const float2 nz = make_float2(-0.0f, -0.0f);
+    if (wpx) integrate_kernel<1><<<integrate_grid<1>(), kThreads, 0, st>>>(s, depth, wpx, in, M_d, nz);
+    else integrate_kernel<0><<<integrate_grid<0>(), kThreads, 0, st>>>(s, depth, nullptr, in, M_d, nz);
     return cudaGetLastError();
 }
 

@@ -107,6 +107,7 @@ struct SceneDev {
     int nb, ne, nv;
     int ovf_cap;
     float voxel_size, mu, z_min, z_max;
+    float inv_mu;  // RN(1 / mu)
     int max_w, weight_mode;
 };
 

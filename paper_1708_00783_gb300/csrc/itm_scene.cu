@@ -133,6 +133,7 @@ int itm_scene_create(const itm_scene_params *params, itm_scene **out)
     d.ovf_cap = overflow_capacity();
     d.voxel_size = params->voxel_size;
     d.mu = params->mu;
+    d.inv_mu = 1.0f / params->mu;  // IEEE float division: RN(1 / mu)
     d.z_min = params->z_min;
     d.z_max = params->z_max;
     d.max_w = params->max_w;
