@@ -1,18 +1,24 @@
-"""Batched per-frame core (submaps, many scenes) against the single-scene path.
+"""Batched per-frame core (submaps, many scenes) against the CPU oracle and the
+single-scene path.
 
-A scene processed inside a batch must end up bit-identical to the same scene
-processed alone with itm_allocate / itm_integrate / itm_raycast: the same
-allocated blocks, voxels and raycast images -- with the captured CUDA graph
-and without, for scenes of different resolutions, voxel sizes and hash sizes
-in one batch, and for one frame fused into several submaps at their relative
-poses (InfiniTAM v3 Sec. 7.2).
+Every scene processed inside a batch is run through the oracle on the same
+frames, crops and poses (a submap at its submap-relative pose), and its
+allocated blocks, weights, voxels and raycast images must meet the parity bar
+against the oracle's.  It must also end up bit-identical to the same scene
+processed alone with itm_allocate / itm_integrate / itm_raycast -- with the
+captured CUDA graph and without, for scenes of different resolutions, voxel
+sizes and hash sizes in one batch, and for one frame fused into several
+submaps at their relative poses (InfiniTAM v3 Sec. 7.2).
 """
+
+import subprocess
 
 import numpy as np
 import pytest
 
-from synth import Intrinsics, kinect_workload, tiny_workload
-from tests.parity_util import compare_volumes
+import oracle
+from synth import Intrinsics, batched, kinect_workload, tiny_workload
+from tests.parity_util import compare_raycast, compare_volumes
 
 pytestmark = pytest.mark.gpu
 
@@ -36,16 +42,33 @@ def crop(frame_depth, intr, W, H):
     return np.ascontiguousarray(frame_depth[v0:v0 + H, u0:u0 + W]), ci
 
 
+def small_room():
+    """The first 80x60 room of the batched workload's 64 independent scenes
+    (with its own voxel size, mu = 4 voxels)."""
+    return next(w for w in batched.small_scenes() if w.intr.width == 80)
+
+
 def scene_specs():
     """(workload, params, crop size) of scenes with uneven sizes."""
     tiny = tiny_workload()
     room = kinect_workload(seed=5)
+    small = small_room()
     return [
         (tiny, dict(tiny.params), (160, 120)),
         (tiny, dict(tiny.params, num_buckets=1 << 8, num_excess=1 << 13), (96, 72)),
         (room, dict(room.params, num_buckets=1 << 16, num_blocks=1 << 17), (320, 240)),
         (room, dict(room.params, voxel_size=0.008, mu=0.032, num_buckets=1 << 18, num_blocks=1 << 17), (640, 480)),
+        (small, dict(small.params), (80, 60)),
     ]
+
+
+def oracle_scene(params):
+    """The oracle for one scene: the OpenMP build where there is one (its
+    results are byte-identical to the single-threaded build's)."""
+    try:
+        return oracle.Scene(**params, threaded=True)
+    except (OSError, subprocess.CalledProcessError):
+        return oracle.Scene(**params)
 
 
 def as_intr(itm, c):
@@ -60,10 +83,11 @@ def test_batch_equals_single_scene_path(itm, use_graph):
     itm.itm_batch_set_graph(batch, use_graph)
     batched = [itm.Scene(**p) for _, p, _ in specs]
     alone = [itm.Scene(**p) for _, p, _ in specs]
+    orcs = [oracle_scene(p) for _, p, _ in specs]
     stream = torch.cuda.Stream()
     for k in range(4):
         items, refs = [], []
-        for (w, p, (W, H)), sb, sa in zip(specs, batched, alone):
+        for (w, p, (W, H)), sb, sa, so in zip(specs, batched, alone, orcs):
             f = w.frame(k)
             d, ci = crop(f.depth, w.intr, W, H)
             D = dev(d)
@@ -73,22 +97,27 @@ def test_batch_equals_single_scene_path(itm, use_graph):
             va = torch.zeros_like(vb)
             na = torch.zeros_like(vb)
             items.append((sb.handle, D, intr, f.T_wc, vb, nb))
-            refs.append((sa, D, intr, f.T_wc, va, na, vb, nb))
+            refs.append((sa, so, d, ci, D, intr, f.T_wc, va, na, vb, nb))
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             itm.itm_batch_run(batch, items, stream=stream)
         stream.synchronize()
-        for sa, D, intr, T, va, na, vb, nb in refs:
+        for sa, so, d, ci, D, intr, T, va, na, vb, nb in refs:
             sa.allocate(D, intr, T)
             sa.integrate(D, intr, T)
             sa.raycast(intr, T, va, na)
         torch.cuda.synchronize()
-        for sa, D, intr, T, va, na, vb, nb in refs:
+        for sa, so, d, ci, D, intr, T, va, na, vb, nb in refs:
             assert torch.equal(va, vb) and torch.equal(na, nb)
-    for sb, sa in zip(batched, alone):
+            # the batch against the oracle on the same crop and pose
+            _, _, (vo, no) = so.process(d, ci.as_array(), T)
+            assert so.status == 0
+            compare_raycast(vb.cpu().numpy(), nb.cpu().numpy(), vo, no, T)
+    for sb, sa, so in zip(batched, alone, orcs):
         assert sb.status() == 0 and sa.status() == 0
         rep = compare_volumes(sb.export(), sa.export())
         assert rep["sdf_bitexact_frac"] == 1.0
+        compare_volumes(sb.export(), so.export())
         st_b, st_a = sb.stats(), sa.stats()
         assert st_b["updated_voxels"] == st_a["updated_voxels"] and st_b["frames"] == st_a["frames"] == 4
     itm.itm_batch_destroy(batch)
@@ -115,13 +144,15 @@ def submap_poses(n, seed=3):
 
 def test_one_frame_fused_into_submaps(itm):
     """One depth frame (one device buffer) fused into three submaps at their
-    relative poses in one batch; each submap matches its own single-scene run."""
+    relative poses in one batch; each submap matches its own single-scene run
+    and the oracle run at the submap-relative pose."""
     import torch
     w = kinect_workload(seed=9)
     p = dict(w.params, num_buckets=1 << 18, num_blocks=1 << 18)
     P = submap_poses(3)
     subs_b = [itm.Scene(**p) for _ in P]
     subs_a = [itm.Scene(**p) for _ in P]
+    subs_o = [oracle_scene(p) for _ in P]
     batch = itm.itm_batch_create(4)
     stream = torch.cuda.Stream()
     ci = as_intr(itm, w.intr)
@@ -140,14 +171,19 @@ def test_one_frame_fused_into_submaps(itm):
         with torch.cuda.stream(stream):
             itm.itm_batch_run(batch, items, stream=stream)
         stream.synchronize()
-        for (T, vb, nb), sa in zip(outs, subs_a):
+        for (T, vb, nb), sa, so in zip(outs, subs_a, subs_o):
             va = torch.zeros_like(vb)
             na = torch.zeros_like(vb)
             sa.process(D, ci, T, va, na)
             torch.cuda.synchronize()
             assert torch.equal(va, vb) and torch.equal(na, nb)
-    for sb, sa in zip(subs_b, subs_a):
-        compare_volumes(sb.export(), sa.export())
+            _, _, (vo, no) = so.process(f.depth, w.intr.as_array(), T)
+            assert so.status == 0
+            compare_raycast(vb.cpu().numpy(), nb.cpu().numpy(), vo, no, T)
+    for sb, sa, so in zip(subs_b, subs_a, subs_o):
+        rep = compare_volumes(sb.export(), sa.export())
+        assert rep["sdf_bitexact_frac"] == 1.0
+        compare_volumes(sb.export(), so.export())
     itm.itm_batch_destroy(batch)
 
 
