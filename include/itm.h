@@ -445,6 +445,9 @@ const char *itm_version(void);
 
 /* Distinct blocks one itm_frame_blocks_noalloc call can hold. */
 #define ITM_NOALLOC_MAX_BLOCKS (1 << 21)
+/* Flag bits of itm_frame_blocks_noalloc's count (the low 30 bits count blocks). */
+#define ITM_NOALLOC_RANGE 0x40000000
+#define ITM_NOALLOC_OVERFLOW ((int32_t)0x80000000u)
 
 /* The voxel blocks one depth frame touches, computed without allocating
  * memory.  The paper has no counterpart: this serves callers that cannot
@@ -458,21 +461,28 @@ const char *itm_version(void);
  * scene with these parameters (the segment d - mu .. d + mu of every pixel
  * with z_min <= d <= z_max, every block crossed), in no particular order, as
  * int16 (x, y, z) triples in coords_dev (caller device memory, cap triples);
- * *count_dev (caller device memory) receives the number of distinct blocks,
- * which may exceed cap (then only cap are written).  A negative count means
- * the fixed set overflowed (excluded by the size check below).
+ * *count_dev (caller device memory) receives in its low 30 bits the number of
+ * distinct blocks, which may exceed cap (then only cap are written).  Bit 30
+ * (ITM_NOALLOC_RANGE) is set when a pixel's segment left the int16 block
+ * coordinates and the pixel was dropped (itm_allocate reports the same case
+ * as ITM_ST_RANGE); bit 31 (a negative count, ITM_NOALLOC_OVERFLOW) when a
+ * block found no slot in the fixed set within its probe limit (not expected
+ * below the size check).
  *
  * Memory: the de-duplication set is a fixed device array of
  * 2 * ITM_NOALLOC_MAX_BLOCKS 64-bit words (32 MiB) inside the library,
  * present on every GPU that loads the library until the process exits.
  * The first call on a device looks up that array's address (with the
- * device current); make that first call before any stream capture.  Each
+ * device current) and keeps it for the life of the process; make that first
+ * call before any stream capture, and do not use the entry point across a
+ * cudaDeviceReset.  Each
  * call clears the array and the count before use.  All calls share the
  * array: calls that overlap on the GPU (other streams, other host threads)
  * race and give wrong results.
  *
- * Errors: ITM_ERR_ARG for null pointers, invalid intrinsics, parameters or
- * a non-finite pose; ITM_ERR_TOO_LARGE when width * height * (the most
+ * Errors: ITM_ERR_ARG for null pointers, invalid intrinsics, parameters, a
+ * non-finite pose or one that is not rigid (last row 0 0 0 1, rotation rows
+ * orthonormal within 1e-4); ITM_ERR_TOO_LARGE when width * height * (the most
  * blocks one pixel's segment can cross) exceeds ITM_NOALLOC_MAX_BLOCKS;
  * ITM_ERR_CUDA when a CUDA call fails.  Asynchronous on `stream`. */
 int itm_frame_blocks_noalloc(const float *depth_dev, const itm_intrinsics *intr, const float T_wc[16],

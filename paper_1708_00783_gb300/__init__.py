@@ -28,6 +28,8 @@ ERRORS = {1: "ITM_ERR_ARG", 2: "ITM_ERR_CUDA", 3: "ITM_ERR_HASH_FULL", 4: "ITM_E
 (ITM_ERR_ARG, ITM_ERR_CUDA, ITM_ERR_HASH_FULL, ITM_ERR_VBA_FULL, ITM_ERR_RANGE, ITM_ERR_TIMEOUT, ITM_ERR_OVERFLOW,
  ITM_ERR_TOO_LARGE, ITM_ERR_SINGULAR, ITM_ERR_BOUNDS) = range(1, 11)
 ITM_NOALLOC_MAX_BLOCKS = 1 << 21
+ITM_NOALLOC_RANGE = 1 << 30      # count bit: a pixel left the int16 block range
+ITM_NOALLOC_OVERFLOW = -(1 << 31)  # count bit 31 (a negative count): the fixed set overflowed
 ITM_MLP_FEATURES, ITM_MLP_HIDDEN, ITM_MLP_PARAMS = 52, 64, 7617
 ITM_MLP_PACKED_BYTES, ITM_MLP_SCRATCH_PER_SAMPLE = 17168, 257
 ITM_BATCH_STAGES = 6
@@ -455,7 +457,14 @@ def itm_version() -> str:
 
 def itm_frame_blocks_noalloc(depth, intr, T_wc, voxel_size, mu, z_min, z_max, coords, cap, count, stream=None):
     """Blocks one depth frame touches, into caller buffers (coords: device
-    int16 [cap, 3]; count: device int32 [1]); the library allocates nothing."""
+    int16 [cap, 3]; count: device int32 [1], the block count in its low 30
+    bits with the ITM_NOALLOC_RANGE / ITM_NOALLOC_OVERFLOW flags); the library
+    allocates nothing.  Every buffer is checked (device, dtype, contiguity,
+    size) before the call."""
+    import torch
+    _buffer(depth, _f32_t(), _pixels(intr), "itm_frame_blocks_noalloc: depth")
+    _buffer(coords, torch.int16, 3 * max(0, int(cap)), "itm_frame_blocks_noalloc: coords")
+    _buffer(count, torch.int32, 1, "itm_frame_blocks_noalloc: count")
     a, p = _pose(T_wc)
     _check(_lib.itm_frame_blocks_noalloc(_ptr(depth), ctypes.byref(intr), p, float(voxel_size), float(mu),
                                          float(z_min), float(z_max), _ptr(coords), int(cap), _ptr(count),

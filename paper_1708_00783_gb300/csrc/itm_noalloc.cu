@@ -14,13 +14,15 @@
 // code must not pass the array's name to a kernel (on the host it names a
 // stand-in, not device memory): the first call on each device looks up its
 // device address with cudaGetSymbolAddress, with that device current, and
-// keeps it.  Every call shares the array and clears it first; calls that
-// overlap on the GPU (different streams, or a second host thread) race on it.
+// keeps it (so the entry point must not be used across a cudaDeviceReset,
+// which frees the array behind that address).  Every call shares the array
+// and clears it first; calls that overlap on the GPU (different streams, or a
+// second host thread) race on it.
 #include <math.h>
 
 #include <mutex>
 
-#include "itm_internal.cuh"
+#include "itm_ops.cuh"
 
 namespace itm {
 
@@ -64,10 +66,15 @@ __device__ __forceinline__ uint32_t slot_of(unsigned long long k)
     return (uint32_t)k & (uint32_t)(kSlots - 1);
 }
 
+constexpr int kMaxProbes = 256;             // linear probes before a key gives up (load <= 1/2)
+constexpr uint32_t kCountOverflow = 0x80000000u;  // *count bit: the fixed set overflowed
+constexpr uint32_t kCountRange = 0x40000000u;     // *count bit: a pixel left the int16 block range
+constexpr uint32_t kCountMask = 0x3fffffffu;
+
 // One thread per pixel, 8x4-pixel warp tiles; the segment d-mu .. d+mu and
-// the DDA over the blocks it crosses are the same arithmetic as
-// alloc_enumerate_kernel (Sec. 4.2).  Each distinct block enters the set
-// once and is appended to the caller's output.
+// the walk over the blocks it crosses are the allocation's own
+// (segment_walk_setup / segment_walk_step, Sec. 4.2).  Each distinct block
+// enters the set once and is appended to the caller's output.
 __global__ void __launch_bounds__(256) frame_blocks_kernel(unsigned long long *__restrict__ set,
                                                            const float *__restrict__ depth, Intr in, Mat34 T,
                                                            float inv_b, float mu, float z_min, float z_max,
@@ -78,50 +85,18 @@ __global__ void __launch_bounds__(256) frame_blocks_kernel(unsigned long long *_
     const int v = blockIdx.y * 8 + (warp >> 2) * 4 + (lane >> 3);
     float d = 0.0f;
     if (u < in.W && v < in.H) d = __ldg(&depth[(size_t)v * in.W + u]);
-    bool more = (d > 0.0f) && !(d < z_min) && !(d > z_max);
-    int cur[3] = {0, 0, 0}, step[3] = {0, 0, 0}, left[3] = {0, 0, 0};
-    float tmax[3] = {0.f, 0.f, 0.f}, tdelta[3] = {0.f, 0.f, 0.f};
-    if (more) {
-        const float rx = fdiv(fsub((float)u, in.cx), in.fx);
-        const float ry = fdiv(fsub((float)v, in.cy), in.fy);
-        float z0 = fsub(d, mu);
-        const float z1 = fadd(d, mu);
-        if (z0 < 1e-3f) z0 = 1e-3f;
-        const float ax = fmul(rx, z0), ay = fmul(ry, z0);
-        const float bx = fmul(rx, z1), by = fmul(ry, z1);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const float q0 = fmul(row_apply(&T.m[4 * i], ax, ay, z0), inv_b);
-            const float q1 = fmul(row_apply(&T.m[4 * i], bx, by, z1), inv_b);
-            const float f0 = floorf(q0), f1 = floorf(q1);
-            if (!(f0 >= -32768.0f && f0 <= 32767.0f && f1 >= -32768.0f && f1 <= 32767.0f)) {
-                more = false;
-                continue;
-            }
-            cur[i] = (int)f0;
-            const int end = (int)f1;
-            const float dir = fsub(q1, q0);
-            if (end > cur[i]) {
-                step[i] = 1;
-                left[i] = end - cur[i];
-                tdelta[i] = fdiv(1.0f, dir);
-                tmax[i] = fdiv(fsub((float)(cur[i] + 1), q0), dir);
-            } else if (end < cur[i]) {
-                step[i] = -1;
-                left[i] = cur[i] - end;
-                tdelta[i] = fdiv(-1.0f, dir);
-                tmax[i] = fdiv(fsub((float)cur[i], q0), dir);
-            }
-        }
-    }
+    SegmentWalk g;
+    const int seg = segment_walk_setup(u, v, d, in, T, inv_b, mu, z_min, z_max, g);
+    if (seg == kSegRange) atomicOr(reinterpret_cast<unsigned int *>(count), kCountRange);
+    bool more = seg == kSegWalk;
     while (__any_sync(kFull, more)) {
-        const unsigned long long key = more ? pack_key(cur[0], cur[1], cur[2]) : 0ull;
+        const unsigned long long key = more ? pack_key(g.cur[0], g.cur[1], g.cur[2]) : 0ull;
         const unsigned peers = __match_any_sync(kFull, key);
         if (more && lane == __ffs(peers) - 1) {
-            uint32_t s = slot_of(key);
+            uint32_t slot = slot_of(key);
             bool fresh = false, placed = false;
-            for (int probe = 0; probe < kSlots; ++probe) {
-                const unsigned long long old = atomicCAS(&set[s], 0ull, key);
+            for (int probe = 0; probe < kMaxProbes; ++probe) {
+                const unsigned long long old = atomicCAS(&set[slot], 0ull, key);
                 if (old == 0ull) {
                     fresh = placed = true;
                     break;
@@ -130,32 +105,34 @@ __global__ void __launch_bounds__(256) frame_blocks_kernel(unsigned long long *_
                     placed = true;
                     break;
                 }
-                s = (s + 1) & (uint32_t)(kSlots - 1);
+                slot = (slot + 1) & (uint32_t)(kSlots - 1);
             }
-            if (!placed) atomicOr(reinterpret_cast<unsigned int *>(count), 0x80000000u);  // cannot happen below kMaxBlocks
+            if (!placed) atomicOr(reinterpret_cast<unsigned int *>(count), kCountOverflow);
             if (fresh) {
-                const int p = warp_append(count);
-                if (p >= 0 && p < cap) {
-                    coords[3 * p + 0] = (short)cur[0];
-                    coords[3 * p + 1] = (short)cur[1];
-                    coords[3 * p + 2] = (short)cur[2];
+                const int p = (int)((uint32_t)warp_append(count) & kCountMask);
+                if (p < cap) {
+                    coords[3 * p + 0] = (short)g.cur[0];
+                    coords[3 * p + 1] = (short)g.cur[1];
+                    coords[3 * p + 2] = (short)g.cur[2];
                 }
             }
         }
-        if (more) {
-            if (left[0] + left[1] + left[2] == 0) {
-                more = false;
-            } else {
-                int a = -1;
-#pragma unroll
-                for (int i = 0; i < 3; ++i)
-                    if (left[i] > 0 && (a < 0 || tmax[i] < tmax[a])) a = i;
-                cur[a] += step[a];
-                tmax[a] = fadd(tmax[a], tdelta[a]);
-                left[a] -= 1;
-            }
-        }
+        if (more) more = segment_walk_step(g);
     }
+}
+
+// A rigid camera-to-world pose: last row 0 0 0 1 and orthonormal rotation
+// rows (within float rounding); the size bound below assumes it.
+bool rigid_pose(const float T[16])
+{
+    if (T[12] != 0.0f || T[13] != 0.0f || T[14] != 0.0f || T[15] != 1.0f) return false;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double dot = 0.0;
+            for (int k = 0; k < 3; ++k) dot += (double)T[4 * i + k] * (double)T[4 * j + k];
+            if (fabs(dot - (i == j ? 1.0 : 0.0)) > 1e-4) return false;
+        }
+    return true;
 }
 
 // Upper bound on the distinct blocks a frame can touch: per pixel the DDA
@@ -191,6 +168,7 @@ extern "C" int itm_frame_blocks_noalloc(const float *depth_dev, const itm_intrin
     if (!(voxel_size > 0.0f) || !(mu > 0.0f) || !(z_min > 0.0f) || !(z_max > z_min)) return ITM_ERR_ARG;
     for (int i = 0; i < 16; ++i)
         if (!isfinite(T_wc[i])) return ITM_ERR_ARG;
+    if (!rigid_pose(T_wc)) return ITM_ERR_ARG;
     if (block_bound(intr, voxel_size, mu) > (double)kMaxBlocks) return ITM_ERR_TOO_LARGE;  // beyond the fixed scratch
     unsigned long long *set = nullptr;
     int r = set_address(&set);

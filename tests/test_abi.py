@@ -196,3 +196,38 @@ def test_host_hash_on_a_million_triples():
         assert np.array_equal(got, want)
         sample = xyz[:2000]
         assert all(oracle.hash_index(x, y, z, nb) == want[i] for i, (x, y, z) in enumerate(sample))
+
+
+_POSE_CHILD = r'''
+import ctypes, sys
+import numpy as np
+import paper_1708_00783_gb300 as itm
+intr = itm.make_intrinsics(64, 48, 60.0, 60.0, 31.5, 23.5)
+R = np.array([[0.36, 0.48, -0.8], [-0.8, 0.6, 0.0], [0.48, 0.64, 0.6]])
+def call(T):
+    T = np.ascontiguousarray(T, dtype=np.float32).ravel()
+    p = T.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+    fake = ctypes.c_void_p(0x1000)  # never dereferenced: the host checks come first
+    return itm._lib.itm_frame_blocks_noalloc(fake, ctypes.byref(intr), p, 0.01, 0.04, 0.2, 5.0, fake, 16, fake, None)
+rigid = np.eye(4); rigid[:3, :3] = R; rigid[:3, 3] = [0.5, -1.0, 2.0]
+scaled = rigid.copy(); scaled[:3, :3] *= 3.0
+sheared = rigid.copy(); sheared[0, 1] += 0.2
+projective = rigid.copy(); projective[3, 2] = 0.1
+for name, T in (("rigid", rigid), ("scaled", scaled), ("sheared", sheared), ("projective", projective)):
+    print(name, call(T), flush=True)
+'''
+
+
+def test_noalloc_rejects_a_pose_that_is_not_rigid():
+    """itm_frame_blocks_noalloc bounds its work by assuming a rigid pose; a
+    scaled, sheared or projective pose is refused with ITM_ERR_ARG on the
+    host, before any CUDA call (this host has no GPU: a rigid pose gets as far
+    as the device lookup and fails there with ITM_ERR_CUDA)."""
+    import subprocess
+    import sys
+    import paper_1708_00783_gb300 as itm
+    r = subprocess.run([sys.executable, "-c", _POSE_CHILD], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stdout[-400:] + r.stderr[-400:]
+    got = {k: int(v) for k, v in (ln.split() for ln in r.stdout.splitlines())}
+    assert got["scaled"] == got["sheared"] == got["projective"] == itm.ITM_ERR_ARG
+    assert got["rigid"] != itm.ITM_ERR_ARG

@@ -109,3 +109,35 @@ def test_batch_items_checked():
         with pytest.raises(itm.ItmError) as e:
             itm.make_batch_items([(2, d, INTR, T, None, None), bad])
         assert e.value.code == itm.ITM_ERR_ARG and "batch item 1" in str(e.value)
+
+
+def test_noalloc_call_checks_its_buffers(monkeypatch):
+    """itm_frame_blocks_noalloc checks depth, coords and count like the Scene
+    calls do: a host or numpy buffer, the wrong dtype or too small a buffer
+    never reaches the library."""
+    reached = []
+
+    class Lib:
+        def itm_frame_blocks_noalloc(self, *a):
+            reached.append(a)
+            return 0
+
+    monkeypatch.setattr(itm, "_lib", Lib())
+    d, coords, count = cuda_like(H, W), cuda_like(8, 3, dtype=torch.int16), cuda_like(1, dtype=torch.int32)
+    itm.itm_frame_blocks_noalloc(d, INTR, T, 0.01, 0.04, 0.2, 5.0, coords, 8, count, stream=0)
+    assert len(reached) == 1
+    bad_calls = [
+        (torch.zeros(H, W), coords, 8, count),                    # host depth
+        (np.zeros((H, W), np.float32), coords, 8, count),         # numpy depth
+        (cuda_like(H, W, dtype=torch.float64), coords, 8, count),  # wrong dtype
+        (cuda_like(H, W - 1), coords, 8, count),                  # smaller than the image
+        (d, cuda_like(8, 3, dtype=torch.int32), 8, count),        # coords dtype
+        (d, coords, 9, count),                                    # cap beyond coords
+        (d, coords, 8, cuda_like(1, dtype=torch.int64)),          # count dtype
+        (d, coords, 8, torch.zeros(1, dtype=torch.int32)),        # host count
+    ]
+    for depth, c, cap, n in bad_calls:
+        with pytest.raises(itm.ItmError) as e:
+            itm.itm_frame_blocks_noalloc(depth, INTR, T, 0.01, 0.04, 0.2, 5.0, c, cap, n, stream=0)
+        assert e.value.code == itm.ITM_ERR_ARG
+    assert len(reached) == 1

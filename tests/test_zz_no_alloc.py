@@ -43,7 +43,9 @@ def test_noalloc_block_set_equals_scene_allocation_on_consecutive_calls():
         itm.itm_frame_blocks_noalloc(d, ci, f.T_wc, p["voxel_size"], p["mu"], p["z_min"], p["z_max"],
                                      coords, cap, count)
         torch.cuda.synchronize()
-        n = int(count.item())
+        raw = int(count.item())
+        assert raw & ~0x3FFFFFFF == 0, "flags set: %#x" % raw
+        n = raw
         assert 0 < n <= cap
         got = coords[:n].cpu().numpy()
         got_set = {tuple(c) for c in got.tolist()}
@@ -76,3 +78,39 @@ def test_noalloc_rejects_inputs_beyond_its_fixed_set():
     itm.itm_frame_blocks_noalloc(small, cs, np.eye(4), 0.005, 0.02, 0.4, 5.0, coords, 16, count)
     torch.cuda.synchronize()
     assert int(count.item()) > 16
+
+
+def test_noalloc_flags_pixels_beyond_the_int16_block_range_and_refuses_non_rigid_poses():
+    """A camera 5 km from the origin puts every segment outside the int16
+    block coordinates: the pixels are dropped and the count carries
+    ITM_NOALLOC_RANGE, as itm_allocate reports ITM_ST_RANGE for the same frame.
+    A scaled pose (not rigid) is refused before any work."""
+    import torch
+
+    import paper_1708_00783_gb300 as itm
+    from synth import tiny_workload
+
+    w = tiny_workload(n_frames=1)
+    f = w.frame(0)
+    d = _dev(f.depth)
+    ci = _intr(itm, w)
+    p = w.params
+    coords = torch.empty((1024, 3), dtype=torch.int16, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    far = f.T_wc.astype(np.float32).copy()
+    far[0, 3] += 5000.0
+    itm.itm_frame_blocks_noalloc(d, ci, far, p["voxel_size"], p["mu"], p["z_min"], p["z_max"], coords, 1024, count)
+    torch.cuda.synchronize()
+    raw = int(count.item())
+    assert raw & itm.ITM_NOALLOC_RANGE
+    assert raw & 0x3FFFFFFF == 0
+    ref = itm.Scene(**p)
+    ref.allocate(d, ci, far)
+    assert ref.status() & 0x4  # ITM_ST_RANGE
+    ref.close()
+    scaled = f.T_wc.astype(np.float32).copy()
+    scaled[:3, :3] *= 2.0
+    with pytest.raises(itm.ItmError) as e:
+        itm.itm_frame_blocks_noalloc(d, ci, scaled, p["voxel_size"], p["mu"], p["z_min"], p["z_max"],
+                                     coords, 1024, count)
+    assert e.value.code == itm.ITM_ERR_ARG
