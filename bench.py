@@ -144,21 +144,22 @@ def load_peaks():
 
 def integrate_source_hash():
     """Hash of the integration kernel's source: itm_integrate.cu and the
-    integration section of itm_ops.cuh (from integrate_block's comment up to
-    the raycast section), so edits elsewhere keep a capture valid."""
+    integration section of itm_ops.cuh (from the packed-pair helpers up to the
+    raycast section), so edits elsewhere keep a capture valid."""
     csrc = os.path.join(ROOT, "paper_1708_00783_gb300", "csrc")
     with open(os.path.join(csrc, "itm_integrate.cu"), "rb") as f:
         a = f.read()
     with open(os.path.join(csrc, "itm_ops.cuh"), "rb") as f:
         ops = f.read()
-    i = ops.index(b"// Block ptr (coordinates b) for thread t")
+    i = ops.index(b"// Packed pairs of separately rounded float operations")
     j = ops.index(b"// ---------------------------------------------------------------- raycast")
     return hashlib.sha256(a + ops[i:j]).hexdigest()[:16]
 
 
 def committed_traffic():
-    """DRAM bytes per integration launch from the committed ncu summary, if it
-    was taken from the current kernel source."""
+    """The committed ncu summary of the integration's DRAM bytes, if it was
+    taken from the current kernel source: (bytes per launch, the captured
+    frames [first, last], DRAM bytes / algorithmic bytes of those frames)."""
     p = os.path.join(ROOT, "profiles", "integrate_kinect_traffic.json")
     if not os.path.exists(p):
         return None
@@ -166,7 +167,7 @@ def committed_traffic():
         d = json.load(f)
     if d.get("integrate_source_sha256_16") != integrate_source_hash():
         return None
-    return d.get("dram_bytes_per_launch_mean")
+    return d.get("dram_bytes_per_launch_mean"), d.get("frames"), d.get("traffic_over_algorithmic")
 
 
 class ClockSampler:
@@ -880,7 +881,13 @@ def run_ours(args, world, rank, local):
     alg_bytes = 10.0 * updated + 4.0 * n_pix * args.steps + 12.0 * visible_blocks
     achieved = alg_bytes / (integ_ms / 1000.0) / 1e9
     peak, peak_kind = load_peaks()
-    traffic = committed_traffic() if args.workload == "kinect" else None  # captured on the room workload
+    # DRAM bytes per launch from the committed capture of the same timed frames
+    # (room workload, frames warm-up .. warm-up + steps - 1); null when the
+    # kernel changed since, or the frames differ
+    traffic = traffic_ratio = None
+    cap = committed_traffic() if args.workload == "kinect" else None
+    if cap and cap[1] == [args.warmup, args.warmup + args.steps - 1]:
+        traffic, traffic_ratio = cap[0], cap[2]
 
     mesh_rep = None
     if extra and args.mesh:
@@ -1029,6 +1036,7 @@ def run_ours(args, world, rank, local):
             "unit": "GB/s",
             "frac": achieved / peak,
             "traffic": traffic,
+            "traffic_over_algorithmic": traffic_ratio,
             "algorithmic_bytes_per_launch": alg_bytes / args.steps,
             "launch_ms_mean": integ_ms / args.steps,
         },

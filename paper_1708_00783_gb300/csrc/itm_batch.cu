@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(64) batch_integrate_kernel(const ItemDev *__re
         const int ptr = __ldg(&it.s.visible[vb - prefix[k]]);
         const short4 b = __ldg(&it.s.block_pos[ptr]);
         unsigned updated = 0;
-        short4 unused = b;
-        integrate_block<0>(it.s, it.depth, nullptr, it.in, it.M, ptr, b, t, updated, false, 0, unused, rcp_w, nz);
+        const RowData row = load_row<0>(it.s, ptr, t);
+        integrate_block<0>(it.s, it.depth, nullptr, it.in, it.M, ptr, b, t, updated, row, rcp_w, nz);
         for (int o = 16; o > 0; o >>= 1) updated += __shfl_xor_sync(kFull, updated, o);
         if ((t & 31) == 0 && updated) atomicAdd(&it.s.ctr->updated, (unsigned long long)updated);
     }

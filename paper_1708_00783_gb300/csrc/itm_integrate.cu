@@ -5,8 +5,8 @@
 // iteration; thread t owns the x-row of voxels 8t .. 8t+7 (y = t & 7,
 // z = t >> 3): 32 contiguous bytes of sdf and 8 of weights, so each warp
 // covers four z-slices with fully coalesced 16-byte accesses.  The next
-// block's index and coordinates are fetched while the current one is
-// processed.
+// block's index, coordinates and row data are requested before the current
+// block is processed (a two-stage software pipeline over the visible list).
 //
 // Each voxel runs the listing computeUpdatedVoxelDepthInfo with IEEE
 // round-to-nearest results in the listing's order (no product fused into a
@@ -52,20 +52,29 @@ __global__ void __launch_bounds__(kThreads) integrate_kernel(SceneDev s, const f
     int i = blockIdx.x;
     int ptr = 0;
     short4 b = make_short4(0, 0, 0, 0);
+    RowData row;
     if (i < n) {
         ptr = __ldg(&s.visible[i]);
         b = __ldg(&s.block_pos[ptr]);
+        row = load_row<MODE>(s, ptr, t);
     }
     while (i < n) {
-        // the next block's index now, its coordinates during this block's update
+        // the next block's index, coordinates and row data are requested
+        // before this block's update, which hides their latency
         const int i_next = i + gridDim.x;
         int ptr_next = 0;
-        if (i_next < n) ptr_next = __ldg(&s.visible[i_next]);
         short4 b_next = b;
-        integrate_block<MODE>(s, depth, wpx, in, M, ptr, b, t, updated, i_next < n, ptr_next, b_next, rcp_w, nz);
+        RowData row_next = row;
+        if (i_next < n) {
+            ptr_next = __ldg(&s.visible[i_next]);
+            b_next = __ldg(&s.block_pos[ptr_next]);
+            row_next = load_row<MODE>(s, ptr_next, t);
+        }
+        integrate_block<MODE>(s, depth, wpx, in, M, ptr, b, t, updated, row, rcp_w, nz);
         i = i_next;
         ptr = ptr_next;
         b = b_next;
+        row = row_next;
     }
 
     // counters: one atomic per warp

@@ -16,14 +16,25 @@ import bench  # noqa: E402
 def test_committed_traffic_follows_the_integration_source(monkeypatch):
     with open(os.path.join(ROOT, "profiles", "integrate_kinect_traffic.json")) as f:
         d = json.load(f)
+    want = (d["dram_bytes_per_launch_mean"], d["frames"], d["traffic_over_algorithmic"])
     if d["integrate_source_sha256_16"] == bench.integrate_source_hash():
-        assert bench.committed_traffic() == d["dram_bytes_per_launch_mean"] > 0
+        assert bench.committed_traffic() == want and want[0] > 0
     else:  # the kernel changed since the capture: no traffic is reported
         assert bench.committed_traffic() is None
     monkeypatch.setattr(bench, "integrate_source_hash", lambda: d["integrate_source_sha256_16"])
-    assert bench.committed_traffic() == d["dram_bytes_per_launch_mean"]
+    assert bench.committed_traffic() == want
     monkeypatch.setattr(bench, "integrate_source_hash", lambda: "0" * 16)
     assert bench.committed_traffic() is None
+
+
+def test_committed_traffic_pairs_the_same_frames():
+    """The summary's ratio is DRAM bytes over the algorithmic bytes of the
+    same launches: the bench's default timed frames (warm-up 5, 20 steps)."""
+    with open(os.path.join(ROOT, "profiles", "integrate_kinect_traffic.json")) as f:
+        d = json.load(f)
+    assert d["frames"] == [5, 24] and d["captured_launches"] == 20
+    assert abs(d["dram_bytes_per_launch_mean"] / d["algorithmic_bytes_per_launch_same_frames"]
+               - d["traffic_over_algorithmic"]) < 1e-3
 
 
 def test_peak_from_the_measured_file_else_the_fallback(tmp_path, monkeypatch):
