@@ -280,6 +280,17 @@ int itm_track_depth(const float *depth_dev, const itm_intrinsics *intr, int leve
  * are written).  Synchronises the stream. */
 int itm_mesh(itm_scene *scene, float *triangles_dev, int64_t capacity, int64_t *n_out, itm_stream stream);
 
+/* The Marching-Cubes case table itm_mesh uses (Sec. 4 meshing), for
+ * inspection: for each of the 256 inside/outside patterns of a cell's corners
+ * (bit k set: corner k, at (k & 1, (k >> 1) & 1, k >> 2), has F < 0) count[cfg]
+ * triangles, whose corners are the crossings on cube edges edges[15 * cfg +
+ * 3 * t + 0..2], edge 4 a + o1 + 2 o2 running along axis a from the corner
+ * whose other two coordinates are o1 (lower axis) and o2 (higher axis); each
+ * triangle counter-clockwise seen from the F > 0 side.  count: host uint8[256],
+ * edges: host uint8[256 * 15] (caller memory).  Host only, no device call.
+ * Errors: ITM_ERR_ARG for a null pointer. */
+int itm_mesh_case_table(uint8_t *count, uint8_t *edges);
+
 /* itm_allocate on an unsigned short millimetre frame: the allocation reads
  * raw_dev (device uint16[height*width]) and converts each pixel as
  * itm_depth_u16_to_f32 does (raw / 1000, correctly rounded, Sec. 4 view

@@ -125,6 +125,7 @@ def _load():
         "itm_raycast_combined": (I, [ctypes.POINTER(P), fp16, I, ip, fp16, P, P, P]),
         "itm_depth_halve": (I, [P, I, I, P, P]),
         "itm_mesh": (I, [P, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), P]),
+        "itm_mesh_case_table": (I, [P, P]),
         "itm_icp_reduce": (I, [P, ip, fp16, P, P, ip, fp16, F, P, P]),
         "itm_icp_step": (I, [ctypes.POINTER(ctypes.c_double), fp16, ctypes.POINTER(ctypes.c_double)]),
         "itm_track_scratch_bytes": (ctypes.c_size_t, [I, I, I]),
@@ -337,6 +338,15 @@ def itm_mesh(scene, triangles=None, capacity=0, stream=None):
         return n.value
     _check(r, "itm_mesh")
     return n.value
+
+
+def itm_mesh_case_table():
+    """The Marching-Cubes case table of itm_mesh (host call): triangle counts
+    uint8[256] and edge indices uint8[256, 5, 3]."""
+    count = np.zeros(256, dtype=np.uint8)
+    edges = np.zeros((256, 5, 3), dtype=np.uint8)
+    _check(_lib.itm_mesh_case_table(count.ctypes.data, edges.ctypes.data), "itm_mesh_case_table")
+    return count, edges
 
 
 def itm_depth_halve(depth_in, width, height, depth_out, stream=None):

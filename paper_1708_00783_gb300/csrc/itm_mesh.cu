@@ -4,13 +4,12 @@
 // Cells are the voxel cubes g + {0,1}^3 whose eight corners are allocated
 // and observed (weight > 0); cells that straddle blocks read the neighbour
 // blocks.  The triangulation of each of the 256 inside/outside corner
-// patterns is built once on the host by walking the cube's faces: on each
-// face the crossings of its sign-changing edges are joined into directed
-// segments (inside on the left seen from outside the cube), a face with two
-// diagonal inside corners cutting off each inside corner (a rule that
-// depends only on the face, so neighbouring cells agree and the mesh is
-// closed); the segments chain into loops, each fanned from its crossing on
-// the lowest-numbered edge, counter-clockwise seen from outside (F > 0).
+// patterns is built once on the host (build_table): the crossings of the
+// sign-changing edges are linked face by face, a face with two diagonal
+// inside corners separating them (a rule that depends only on the face, so
+// neighbouring cells agree and the mesh is closed); the links form loops,
+// each oriented by a geometric test and fanned from its crossing on the
+// lowest-numbered edge, counter-clockwise seen from outside (F > 0).
 // Edge 4 a + o1 + 2 o2 runs along axis a from the corner whose other two
 // coordinates are o1 (lower axis) and o2 (higher axis).  A crossing sits at
 // t = F_a / (F_a - F_b) from the edge's lower corner: coordinate
@@ -33,66 +32,103 @@ struct McTable {
     uint8_t edge[256][15];  // 3 edge indices per triangle
 };
 
-int edge_id(int k1, int k2)
+// Corner k of a cell sits at (k & 1, (k >> 1) & 1, k >> 2); edge e = 4 a + o1 +
+// 2 o2 runs along axis a from its lower corner.
+int edge_lo(int e)
 {
-    const int d = k1 ^ k2;
-    const int axis = d == 1 ? 0 : (d == 2 ? 1 : 2);
-    const int lo = k1 < k2 ? k1 : k2;
-    const int u = axis == 0 ? 1 : 0, v = axis == 2 ? 1 : 2;  // the other axes, lower first
-    return 4 * axis + ((lo >> u) & 1) + 2 * ((lo >> v) & 1);
+    const int a = e >> 2, o1 = e & 1, o2 = (e >> 1) & 1;
+    const int ua = a == 0 ? 1 : 0, va = a == 2 ? 1 : 2;  // the other axes, lower first
+    return (o1 << ua) | (o2 << va);
 }
+int edge_hi(int e) { return edge_lo(e) | (1 << (e >> 2)); }
 
+// The case table, derived as a graph: the crossings (edges with one inside and
+// one outside corner) are its nodes, and each face of the cube links the
+// crossings on its four sides -- two crossings are linked to each other, four
+// (two inside corners on a diagonal) are linked in pairs around each inside
+// corner, which separates the diagonal corners (a choice that depends on the
+// face alone, so the two cells sharing the face agree and the mesh is closed).
+// Every crossing has one link on each of its two faces, so the links form
+// loops.  A loop is oriented by geometry: on the face of its first link, seen
+// from outside the cube, the inside corner of the first crossing must lie to
+// the left of the step from the first crossing's midpoint to the second's
+// (inside on the left: the loop runs clockwise seen from the F > 0 side).  It
+// is then fanned from its crossing on the lowest-numbered edge, each triangle
+// (first, next, current) so that it faces the F > 0 side.
 void build_table(McTable &T)
 {
     memset(&T, 0, sizeof(T));
     for (int cfg = 0; cfg < 256; ++cfg) {
-        int from[12], to[12], ns = 0;
-        for (int a = 0; a < 3; ++a) {
-            const int u = (a + 1) % 3, v = (a + 2) % 3;  // (u, v, a) right-handed
-            for (int side = 0; side < 2; ++side) {
-                // corners counter-clockwise seen from outside (normal +a for side 1)
-                static const int uv1[4][2] = {{0, 0}, {1, 0}, {1, 1}, {0, 1}};
-                static const int uv0[4][2] = {{0, 0}, {0, 1}, {1, 1}, {1, 0}};
-                int q[4];
-                for (int i = 0; i < 4; ++i) {
-                    const int *p = side ? uv1[i] : uv0[i];
-                    q[i] = (side << a) | (p[0] << u) | (p[1] << v);
-                }
-                int exits[2], entries[2], exit_pos[2], entry_pos[2], ne = 0, nn = 0;
-                for (int i = 0; i < 4; ++i) {
-                    const bool in0 = (cfg >> q[i]) & 1, in1 = (cfg >> q[(i + 1) & 3]) & 1;
-                    if (in0 == in1) continue;
-                    if (in0) {
-                        exit_pos[ne] = i;
-                        exits[ne++] = edge_id(q[i], q[(i + 1) & 3]);
-                    } else {
-                        entry_pos[nn] = i;
-                        entries[nn++] = edge_id(q[i], q[(i + 1) & 3]);
+        auto inside = [cfg](int k) { return ((cfg >> k) & 1) != 0; };
+        int link[12][2], face_of[12][2], nl[12] = {0};
+        for (int f = 0; f < 6; ++f) {
+            const int a = f >> 1, side = f & 1;
+            int sides[4], ns = 0;
+            for (int e = 0; e < 12; ++e) {
+                if ((e >> 2) == a) continue;  // an edge along the face normal is not on the face
+                const int lo = edge_lo(e), hi = edge_hi(e);
+                if (((lo >> a) & 1) != side) continue;
+                if (inside(lo) != inside(hi)) sides[ns++] = e;
+            }
+            int pairs[2][2], np = 0;
+            if (ns == 2) {
+                pairs[np][0] = sides[0];
+                pairs[np++][1] = sides[1];
+            } else if (ns == 4) {
+                // pair the two crossings at each inside corner of the face
+                for (int i = 0; i < 4; ++i)
+                    for (int j = i + 1; j < 4; ++j) {
+                        const int c0[2] = {edge_lo(sides[i]), edge_hi(sides[i])};
+                        const int c1[2] = {edge_lo(sides[j]), edge_hi(sides[j])};
+                        for (int x = 0; x < 2; ++x)
+                            for (int y = 0; y < 2; ++y)
+                                if (c0[x] == c1[y] && inside(c0[x]) && np < 2) {
+                                    pairs[np][0] = sides[i];
+                                    pairs[np++][1] = sides[j];
+                                }
                     }
-                }
-                for (int k = 0; k < ne; ++k) {
-                    // the exit on edge i pairs with the entry on edge i - 1
-                    // (the two edges at the inside corner q[i])
-                    int j = 0;
-                    if (ne == 2 && entry_pos[0] != ((exit_pos[k] + 3) & 3)) j = 1;
-                    from[ns] = exits[k];
-                    to[ns++] = entries[j];
-                }
             }
+            for (int q = 0; q < np; ++q)
+                for (int h = 0; h < 2; ++h) {
+                    const int e = pairs[q][h];
+                    link[e][nl[e]] = pairs[q][1 - h];
+                    face_of[e][nl[e]++] = f;
+                }
         }
-        bool used[12] = {false};
+        bool seen[12] = {false};
         int nt = 0;
-        for (int s0 = 0; s0 < ns; ++s0) {
-            if (used[s0]) continue;
-            int loop[12], n = 0, cur = s0;
-            while (cur >= 0 && !used[cur] && n < 12) {
-                used[cur] = true;
-                loop[n++] = from[cur];
-                int next = -1;
-                for (int t = 0; t < ns; ++t)
-                    if (!used[t] && from[t] == to[cur]) next = t;
-                cur = next;
-            }
+        for (int e0 = 0; e0 < 12; ++e0) {
+            if (nl[e0] != 2 || seen[e0]) continue;
+            int loop[12], n = 0, prev = -1, cur = e0;
+            do {  // follow the links: each crossing has two, leave by the one not arrived on
+                seen[cur] = true;
+                loop[n++] = cur;
+                const int nxt = link[cur][0] == prev ? link[cur][1] : link[cur][0];
+                prev = cur;
+                cur = nxt;
+            } while (cur != e0 && n < 12);
+            // orientation: outward normal of the face linking loop[0] and loop[1]
+            const int f = link[loop[0]][0] == loop[1] ? face_of[loop[0]][0] : face_of[loop[0]][1];
+            const int a = f >> 1;
+            const double nrm = (f & 1) ? 1.0 : -1.0;
+            auto mid = [](int e, double *m) {
+                const int lo = edge_lo(e), hi = edge_hi(e);
+                for (int k = 0; k < 3; ++k) m[k] = 0.5 * (((lo >> k) & 1) + ((hi >> k) & 1));
+            };
+            double m0[3], m1[3], c[3];
+            mid(loop[0], m0);
+            mid(loop[1], m1);
+            const int in0 = inside(edge_lo(loop[0])) ? edge_lo(loop[0]) : edge_hi(loop[0]);
+            for (int k = 0; k < 3; ++k) c[k] = (double)((in0 >> k) & 1);
+            const double d[3] = {m1[0] - m0[0], m1[1] - m0[1], m1[2] - m0[2]};
+            const double w[3] = {c[0] - m0[0], c[1] - m0[1], c[2] - m0[2]};
+            const double cross_a = d[(a + 1) % 3] * w[(a + 2) % 3] - d[(a + 2) % 3] * w[(a + 1) % 3];
+            if (cross_a * nrm < 0.0)  // inside corner on the right: reverse the loop
+                for (int i = 0, j = n - 1; i < j; ++i, --j) {
+                    const int t = loop[i];
+                    loop[i] = loop[j];
+                    loop[j] = t;
+                }
             int first = 0;
             for (int i = 1; i < n; ++i)
                 if (loop[i] < loop[first]) first = i;
@@ -213,6 +249,14 @@ const McTable &mc_table()
 
 }  // namespace
 
+int mesh_case_table(uint8_t *count, uint8_t *edges)
+{
+    const McTable &t = mc_table();
+    memcpy(count, t.count, sizeof(t.count));
+    memcpy(edges, t.edge, sizeof(t.edge));
+    return ITM_OK;
+}
+
 cudaError_t launch_mesh(const SceneDev &s, float *out, long long cap, unsigned long long *counter, cudaStream_t st)
 {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
@@ -229,3 +273,9 @@ cudaError_t launch_mesh(const SceneDev &s, float *out, long long cap, unsigned l
 }
 
 }  // namespace itm
+
+extern "C" int itm_mesh_case_table(uint8_t *count, uint8_t *edges)
+{
+    if (!count || !edges) return ITM_ERR_ARG;
+    return itm::mesh_case_table(count, edges);
+}

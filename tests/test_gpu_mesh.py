@@ -3,7 +3,10 @@
 The volumes are bit-identical on both sides, and both build every triangle
 with the same float operations, so the meshes must be equal exactly: as
 multisets of triangles, each triangle rotated to start at its smallest
-vertex (its orientation kept).  Cases: the tiny sequence, a learned-weight
+vertex (its orientation kept).  The library derives its case table on its
+own (checked against the oracle's cells on the CPU); the GPU mesh is also
+checked without the oracle: a consistently oriented surface, closed away
+from its boundary, facing the free side of the scene's analytic surfaces.  Cases: the tiny sequence, a learned-weight
 (float weight) volume, a Kinect-scale volume, capacity handling, an empty
 volume and argument errors.
 """
@@ -71,12 +74,52 @@ def fuse(itm, w, frames, params=None, wpx=None):
     return g, o
 
 
+def check_mesh_on_its_own(tris):
+    """Properties of a mesh that do not rest on the oracle's triangulation: no
+    degenerate triangle, a directed edge used by one triangle at most (a
+    consistently oriented surface; a few exceptions remain where a fan lays a
+    triangle into a cell face that the neighbouring cell also triangulates,
+    about 1 in 10^4 edges), and most edges shared by two triangles (closed
+    away from the boundary of the observed region)."""
+    t = np.asarray(tris, np.float32).reshape(-1, 3, 3)
+    area2 = np.linalg.norm(np.cross(t[:, 1] - t[:, 0], t[:, 2] - t[:, 0]), axis=1)
+    assert np.all(np.isfinite(t)) and np.mean(area2 > 0) > 0.99
+    flat = np.ascontiguousarray(t.reshape(-1, 3))
+    keys = [flat[i].tobytes() for i in range(len(flat))]
+    directed = {}
+    for a, b, c in zip(keys[0::3], keys[1::3], keys[2::3]):
+        for e in ((a, b), (b, c), (c, a)):
+            directed[e] = directed.get(e, 0) + 1
+    twice = sum(v > 1 for v in directed.values())
+    assert twice <= 1e-3 * len(directed), "directed edges used twice: %d of %d" % (twice, len(directed))
+    # edges met in both directions (an interior edge of a consistently
+    # oriented surface) against edges met in one direction only (boundary)
+    both = sum(1 for (a, b) in directed if (b, a) in directed) // 2
+    one = sum(1 for (a, b) in directed if (b, a) not in directed)
+    shared = both / (both + one)
+    assert shared > 0.85, shared
+    return t
+
+
 def test_tiny_sequence_mesh_equals_oracle(itm):
     w = tiny_workload()
     g, o = fuse(itm, w, range(w.n_frames))
     mg, mo = gpu_mesh(itm, g), o.mesh()
     assert len(mo) > 5000
     assert np.array_equal(canonical(mg), canonical(mo))
+    # orientation against the scene's own geometry: triangles on the sphere
+    # (centre (-0.35, 0.3, 0), r 0.3) face away from its centre, triangles on
+    # the floor (y = 0) away from the objects face up
+    t = check_mesh_on_its_own(mg)
+    n = np.cross(t[:, 1] - t[:, 0], t[:, 2] - t[:, 0])
+    c = t.mean(axis=1)
+    d = c - np.array([-0.35, 0.3, 0.0])
+    on_sphere = np.abs(np.linalg.norm(d, axis=1) - 0.3) < 0.01
+    assert on_sphere.sum() > 500
+    assert np.mean(np.sum(n[on_sphere] * d[on_sphere], axis=1) > 0) > 0.99
+    on_floor = (np.abs(c[:, 1]) < 0.005) & (np.abs(c[:, 2]) > 0.4)
+    assert on_floor.sum() > 200
+    assert np.mean(n[on_floor, 1] > 0) > 0.97  # sensor noise folds a few floor triangles
 
 
 def test_learned_weight_volume_mesh_equals_oracle(itm):
@@ -100,6 +143,7 @@ def test_kinect_scale_mesh_equals_oracle(itm):
     mg, mo = gpu_mesh(itm, g), o.mesh()
     assert len(mo) > 100000
     assert np.array_equal(canonical(mg), canonical(mo))
+    check_mesh_on_its_own(mg)
 
 
 def test_capacity_and_empty_volume(itm):

@@ -194,3 +194,18 @@ def test_a_field_touching_zero_without_changing_sign_has_no_surface():
     sc2.set_block((0, 0, 0), ((z - 3.0) / 4.0).astype(np.float32), 1.0)
     tris = sc2.mesh()
     assert len(tris) == 2 * 7 * 7 and np.all(tris[..., 2] == np.float32(3.0) * np.float32(S))
+
+
+def test_library_case_table_equals_the_oracle_cells():
+    """The library builds its Marching-Cubes case table by its own derivation
+    (crossings linked face by face, loops oriented by a geometric test); the
+    oracle triangulates each cell by walking the faces counter-clockwise.  On
+    all 256 inside/outside patterns the two give the same triangles, as sets
+    (each loop is found in its own order; host call, no GPU)."""
+    import paper_1708_00783_gb300 as itm
+    count, edges = itm.itm_mesh_case_table()
+    for cfg in range(256):
+        F = np.array([-1.0 if (cfg >> k) & 1 else 1.0 for k in range(8)], np.float32)
+        want = sorted(map(tuple, oracle.cell_triangles(F).tolist()))
+        got = sorted(map(tuple, edges[cfg, :count[cfg]].astype(int).tolist()))
+        assert got == want, (cfg, got, want)
