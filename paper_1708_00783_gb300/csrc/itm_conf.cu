@@ -126,6 +126,7 @@ __device__ __forceinline__ bool conf_features(const Depth &D, const Intr &in, fl
 // --------------------------------------------------------------- inference
 
 constexpr int kTW = 16, kTH = 8, kHW = kTW + 6, kHH = kTH + 6;
+constexpr int kSW = 48;  // row stride of a staged depth tile (words; 16 mod 32 banks)
 constexpr int kRows = kTW * kTH;  // pixels per tile = rows of the A operand = TMEM lanes
 static_assert(kRows == 128 && NH == 64, "one M=128, N=64, K=64 product per layer and tile");
 
@@ -147,9 +148,9 @@ __device__ __forceinline__ uint32_t canon_off(int r, int kc) { return (r >> 3) *
 
 // shared-memory matrix descriptor: start >> 4, leading and stride byte
 // offsets >> 4, bit 46 the descriptor version; base offset 0, no swizzle
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t sbo = 1024)
 {
-    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
            (1ull << 46);
 }
 
@@ -158,18 +159,24 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr)
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NH >> 3) << 17) |
                             ((uint32_t)(kRows >> 4) << 24);
 
-// D[128 x 64] (TMEM, fp32) = A[128 x 64] B[64 x 64]^T as four K=16 steps;
-// completion (operands read, D written) arrives on the mbarrier
-__device__ __forceinline__ void mma_layer(uint32_t tmem, uint32_t a, uint32_t b, uint32_t bar)
+__device__ __forceinline__ void mma_step(uint32_t tmem, uint64_t ad, uint64_t bd, bool accumulate)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(kIdesc), "r"(accumulate ? 1u : 0u));
+}
+
+// D[128 x 64] (TMEM, fp32) = A[128 x 64] B[64 x 64]^T as four K=16 steps,
+// plus, with bias_a, the product of the 128 x 16 tile bias_a and the 64 x 16
+// tile bias_b (8-row groups 256 B apart) as a fifth step; completion
+// (operands read, D written) arrives on the mbarrier
+__device__ __forceinline__ void mma_layer(uint32_t tmem, uint32_t a, uint32_t b, uint32_t bar, uint32_t bias_a = 0,
+                                          uint32_t bias_b = 0)
 {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-        const uint64_t ad = smem_desc(a + 256 * k), bd = smem_desc(b + 256 * k);
-        asm volatile(
-            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-            "l"(ad), "l"(bd), "r"(kIdesc), "r"(k > 0 ? 1u : 0u));
-    }
+    for (int k = 0; k < 4; ++k) mma_step(tmem, smem_desc(a + 256 * k), smem_desc(b + 256 * k), k > 0);
+    if (bias_a) mma_step(tmem, smem_desc(bias_a, 256), smem_desc(bias_b, 256), true);
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
                  : "memory");
 }
@@ -239,35 +246,123 @@ __device__ __forceinline__ void tmem_row32(uint32_t taddr, float (&d)[32])
     for (int i = 0; i < 32; ++i) d[i] = __uint_as_float(r[i]);
 }
 
-// dynamic shared memory: W1, W2 and the A tile in the canonical layout, then
-// b1, b2, w3, b3 (fp32), the depth tile with its halo and the valid flags
+// dynamic shared memory: W1, W2 and two A tiles in the canonical layout, the
+// layer-2 bias tiles, then w3, b3 (fp32), two depth tiles with their halo and
+// two sets of valid flags (one per tile slot)
 constexpr size_t kOffSW1 = 0, kOffSW2 = NH * 64 * 2, kOffSA = 2 * NH * 64 * 2;
-constexpr size_t kOffSF = kOffSA + kRows * 64 * 2;
-constexpr size_t kOffSD = kOffSF + (3 * NH + 4) * 4;
-constexpr size_t kOffSV = kOffSD + kHH * kHW * 4;
-constexpr size_t kConfSmem = kOffSV + kRows;
-constexpr int kTmemCols = 64;  // both layers' accumulators, one after the other
-// at most 8 CTAs per SM (228 KB of shared memory, 1 KB reserved per CTA), so
+constexpr size_t kASize = kRows * 64 * 2;
+constexpr size_t kOffSBA = kOffSA + 2 * kASize;          // 128 x 16 bf16: rows [1, 1, 1, 0, ...]
+constexpr size_t kOffSBB = kOffSBA + kRows * 16 * 2;     // 64 x 16 bf16: rows [b2 split in three, 0, ...]
+constexpr size_t kOffSF = kOffSBB + NH * 16 * 2;         // w3 (64), b3
+constexpr size_t kOffSD = kOffSF + (NH + 4) * 4;
+constexpr size_t kDSize = kHH * kSW * 4;
+constexpr size_t kOffSV = kOffSD + 2 * kDSize;
+constexpr size_t kConfSmem = kOffSV + 2 * kRows;
+constexpr int kTmemCols = 128;  // two tile slots of 64 fp32 accumulator columns
+// at most 4 CTAs per SM (228 KB of shared memory, 1 KB reserved per CTA), so
 // their TMEM columns fit the SM's 512 and no allocation waits
-static_assert(9 * (kConfSmem + 1024) > 228 * 1024 && 8 * kTmemCols <= 512, "TMEM budget");
+static_assert(5 * (kConfSmem + 1024) > 228 * 1024 && 4 * kTmemCols <= 512, "TMEM budget");
+static_assert(NF + 3 <= 64, "three bias columns after the features");
 
+// byte offset of row r, elements 8 kc .. 8 kc + 7, in a 16-wide bf16 operand
+__device__ __forceinline__ uint32_t canon16_off(int r, int kc) { return (r >> 3) * 256 + kc * 128 + (r & 7) * 16; }
+
+// b = hi + mid + lo with three bf16 values (exact for a normal fp32 b: 8
+// significant bits each)
+__device__ __forceinline__ void split3_bf16(float b, __nv_bfloat16 (&o)[3])
+{
+    o[0] = __float2bfloat16_rn(b);
+    const float r1 = b - __bfloat162float(o[0]);
+    o[1] = __float2bfloat16_rn(r1);
+    o[2] = __float2bfloat16_rn(r1 - __bfloat162float(o[1]));
+}
+
+// Tile tile's depth and its 3-pixel halo into sD (kHH rows of kHW values,
+// row stride kSW); 0 outside the image and where D <= 0.
+__device__ __forceinline__ void stage_depth(const float *__restrict__ depth, const Intr &in, int tiles_x, int tile,
+                                            int tid, float *sD)
+{
+    float pre[kStage];
+    fetch_depth(depth, in, tiles_x, tile, tid, pre);
+#pragma unroll
+    for (int j = 0; j < kStage; ++j) {
+        const int i = tid + 128 * j;
+        if (i < kHH * kHW) sD[(i / kHW) * kSW + i % kHW] = pre[j];
+    }
+}
+
+// The pixel's 52 features rounded to bf16, then 1, 1, 1 (the inputs of the
+// three bias columns of W1) and zeros, as row tid of the A tile at sA;
+// returns whether the pixel has depth.
+__device__ __forceinline__ bool write_features(const float *sD, const Intr &in, float rfx, float rfy, float inv_mu,
+                                               int u0, int v0, int tid, unsigned char *sA)
+{
+    const int u = u0 + (tid & (kTW - 1)), v = v0 + tid / kTW;
+    const TileDepth D{sD, u0, v0, kSW};
+    const float dc = D(u, v);
+    const bool ok = u < in.W && v < in.H && dc > 0.0f;
+    float n[3] = {0.0f, 0.0f, 0.0f};
+    if (ok) normal_feature(D, in, rfx, rfy, u, v, n);
+#pragma unroll
+    for (int kc = 0; kc < 8; ++kc) {
+        float f[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int k = 8 * kc + q;
+            f[q] = k < 49 ? patch_feature(D, u, v, dc, inv_mu, k) : (k < NF ? n[k - 49] : 0.0f);
+            if (!ok) f[q] = 0.0f;
+            if (k >= NF && k < NF + 3) f[q] = 1.0f;
+        }
+        *reinterpret_cast<uint4 *>(sA + canon_off(tid, kc)) =
+            make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]), pack_bf16(f[6], f[7]));
+    }
+    return ok;
+}
+
+// relu of two accumulators, rounded to bf16 (relu of the rounded value: the
+// same, as 0 and the rounding are monotone)
+__device__ __forceinline__ uint32_t relu_bf16x2(float a, float b)
+{
+    __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+    p = __hmax2(p, __float2bfloat162_rn(0.0f));
+    return *reinterpret_cast<const uint32_t *>(&p);
+}
+
+// One CTA (one warpgroup of 128 threads) runs its tiles t_0, t_1, ... as a
+// two-slot software pipeline, so that the tensor core and the threads work at
+// the same time:
+//
+//   features(t_0) -> A0; MMA1(t_0)
+//   for each i (slot s = i & 1):
+//     features(t_i+1) -> A[s^1]            while MMA1(t_i) runs
+//     wait MMA1(t_i); h1 = relu(acc) -> A[s]
+//     MMA2(t_i) -> TMEM slot s; MMA1(t_i+1) -> TMEM slot s^1
+//     wait MMA2(t_i); output of t_i       while MMA1(t_i+1) runs
+//
+// Both biases are added by the tensor core: b1 through three extra columns
+// of W1 (its bf16 split) against inputs of 1, b2 through a fifth K=16 step
+// of a constant tile of ones against b2's split.  MMA1 completions arrive on
+// bar1, MMA2 completions on bar2 (one phase per tile each).  One thread waits
+// on each (a bounded number of polls) while the others sit at a barrier; a
+// wait that gives up sends the CTA to its failure path: NaN weights for its
+// remaining pixels (weighted integration skips them), one more bounded wait
+// for each product in flight, then the TMEM is freed.
 __global__ void __launch_bounds__(128) conf_weights_kernel(const float *__restrict__ depth, Intr in, float mu,
                                                            const unsigned char *__restrict__ packed,
                                                            float *__restrict__ wpx, int tiles_x, int n_tiles)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bar;
+    __shared__ __align__(8) uint64_t bar[2];
     __shared__ uint32_t tmem_slot;
-    const float *sB1 = reinterpret_cast<const float *>(smem + kOffSF);
-    const float *sB2 = sB1 + NH, *sW3 = sB2 + NH, *sB3 = sW3 + NH;
-    float *sD = reinterpret_cast<float *>(smem + kOffSD);
-    unsigned char *sValid = smem + kOffSV;
+    const float *sW3 = reinterpret_cast<const float *>(smem + kOffSF);
     const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t sbase = smem_addr(smem), bar_a = smem_addr(&bar);
-    // the next tile's depth is loaded into registers while this one computes
-    // (the first tile's while the weights are staged)
-    float pre[kStage];
-    if (blockIdx.x < n_tiles) fetch_depth(depth, in, tiles_x, blockIdx.x, tid, pre);
+    const uint32_t sbase = smem_addr(smem), bar1 = smem_addr(&bar[0]), bar2 = smem_addr(&bar[1]);
+    auto sA = [&](int slot) { return smem + kOffSA + slot * kASize; };
+    auto sD = [&](int slot) { return reinterpret_cast<float *>(smem + kOffSD + slot * kDSize); };
+    auto sValid = [&](int slot) { return smem + kOffSV + slot * kRows; };
+    const float rfx = 1.0f / in.fx, rfy = 1.0f / in.fy, inv_mu = 1.0f / mu;
+    const int stride = (int)gridDim.x;
+    const int t0 = blockIdx.x;
 
     {
         // weights: 16-byte chunks of the row-major 64 x 64 matrices
@@ -276,132 +371,145 @@ __global__ void __launch_bounds__(128) conf_weights_kernel(const float *__restri
             const int m = j >> 9, n = (j >> 3) & 63, kc = j & 7;
             *reinterpret_cast<uint4 *>(smem + (m ? kOffSW2 : kOffSW1) + canon_off(n, kc)) = __ldg(&W[j]);
         }
-        const float *f32 = reinterpret_cast<const float *>(packed + kOffB1);
+        const float *f32 = reinterpret_cast<const float *>(packed + kOffB1);  // b1, b2, w3, b3
         float *dst = reinterpret_cast<float *>(smem + kOffSF);
-        for (int i = tid; i < 3 * NH + 1; i += 128) dst[i] = f32[i];  // b1, b2, w3, b3 are contiguous
+        for (int i = tid; i < NH + 1; i += 128) dst[i] = f32[2 * NH + i];
+        __syncthreads();  // W1's chunks are in place before their bias columns are written
+        if (tid < NH) {
+            // b1 into W1's columns NF .. NF+2 (bf16 split), b2 into the bias tile
+            __nv_bfloat16 h[3];
+            split3_bf16(f32[tid], h);
+            __nv_bfloat16 *w1row = reinterpret_cast<__nv_bfloat16 *>(smem + kOffSW1 + canon_off(tid, NF / 8));
+            for (int q = 0; q < 3; ++q) w1row[NF % 8 + q] = h[q];
+            split3_bf16(f32[NH + tid], h);
+            __nv_bfloat16 bb[8] = {h[0], h[1], h[2]};
+            for (int q = 3; q < 8; ++q) bb[q] = __float2bfloat16_rn(0.0f);
+            *reinterpret_cast<uint4 *>(smem + kOffSBB + canon16_off(tid, 0)) = *reinterpret_cast<const uint4 *>(bb);
+            *reinterpret_cast<uint4 *>(smem + kOffSBB + canon16_off(tid, 1)) = make_uint4(0u, 0u, 0u, 0u);
+        }
+        // the constant tile: every row [1, 1, 1, 0, ...]
+        const uint32_t one = 0x3F80u;  // bf16 1.0
+        *reinterpret_cast<uint4 *>(smem + kOffSBA + canon16_off(tid, 0)) =
+            make_uint4(one | (one << 16), one, 0u, 0u);
+        *reinterpret_cast<uint4 *>(smem + kOffSBA + canon16_off(tid, 1)) = make_uint4(0u, 0u, 0u, 0u);
     }
-    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar_a) : "memory");
-    async_proxy_fence();
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar1) : "memory");
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar2) : "memory");
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
                      "n"(kTmemCols)
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
+    // the first tile's depth and features
+    stage_depth(depth, in, tiles_x, t0, tid, sD(0));
+    __syncthreads();
+    sValid(0)[tid] = write_features(sD(0), in, rfx, rfy, inv_mu, (t0 % tiles_x) * kTW, (t0 / tiles_x) * kTH, tid,
+                                    sA(0));
+    async_proxy_fence();
     tc_before_sync();
     __syncthreads();
     tc_after_sync();
     const uint32_t tmem = tmem_slot;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * warp) << 16);  // this warp's TMEM lane quarter
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;  // this warp's TMEM lane quarter
+    if (tid == 0) mma_layer(tmem, sbase + kOffSA, sbase + kOffSW1, bar1);
 
-    // A wait that gives up is voted warp-uniform (the TMEM reads are warp
-    // collectives) and reaches the whole CTA at its next barrier.
-    int failed_tile = -1, last_tile = -1;
-    uint32_t failed_parity = 0;
-    bool pending = false;  // this warp's layer-2 wait gave up
-    const float rfx = 1.0f / in.fx, rfy = 1.0f / in.fy, inv_mu = 1.0f / mu;
-    for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int u0 = (tile % tiles_x) * kTW, v0 = (tile / tiles_x) * kTH;
-#pragma unroll
-        for (int j = 0; j < kStage; ++j)
-            if (tid + 128 * j < kHH * kHW) sD[tid + 128 * j] = pre[j];
-        if (tile + (int)gridDim.x < n_tiles) fetch_depth(depth, in, tiles_x, tile + gridDim.x, tid, pre);
-        if (__syncthreads_or(pending)) {
-            failed_tile = last_tile;
-            failed_parity = 1;
+    // products issued and completions consumed on each barrier (thread 0's
+    // counts, for the final wait after a failure)
+    int issued1 = 1, issued2 = 0, done1 = 0, done2 = 0;
+    int fail_from = -1;  // first tile whose output was not written
+    int i = 0;
+    for (int t = t0; t < n_tiles; t += stride, ++i) {
+        const int s = i & 1, tn = t + stride;
+        const bool has_next = tn < n_tiles;
+        const int u0 = (t % tiles_x) * kTW, v0 = (t / tiles_x) * kTH;
+        // the next tile's features while this tile's first product runs
+        if (has_next) {
+            stage_depth(depth, in, tiles_x, tn, tid, sD(s ^ 1));
+            asm volatile("bar.sync 1, 128;" ::: "memory");
+            sValid(s ^ 1)[tid] = write_features(sD(s ^ 1), in, rfx, rfy, inv_mu, (tn % tiles_x) * kTW,
+                                                (tn / tiles_x) * kTH, tid, sA(s ^ 1));
+        }
+        bool ok = true;
+        if (tid == 0) {
+            ok = mbar_wait(bar1, (uint32_t)(done1 & 1));
+            done1 += ok;
+        }
+        if (__syncthreads_or(!ok)) {
+            fail_from = t;
             break;
         }
-        const int u = u0 + (tid & (kTW - 1)), v = v0 + tid / kTW;
-        {
-            // the pixel's features, rounded to bf16, 8 at a time into its A row
-            const TileDepth D{sD, u0, v0, kHW};
-            const float dc = D(u, v);
-            const bool ok = u < in.W && v < in.H && dc > 0.0f;
-            sValid[tid] = ok;
-            float n[3] = {0.0f, 0.0f, 0.0f};
-            if (ok) normal_feature(D, in, rfx, rfy, u, v, n);
+        tc_after_sync();
+        // h1 = bf16(relu(acc)) is layer 2's A tile, in place of x
 #pragma unroll
-            for (int kc = 0; kc < 8; ++kc) {
-                float f[8];
+        for (int half = 0; half < 2; ++half) {
+            float h[32];
+            tmem_row32(tmem + lane_off + 64 * s + 32 * half, h);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int k = 8 * kc + q;
-                    f[q] = k < 49 ? patch_feature(D, u, v, dc, inv_mu, k) : (k < NF ? n[k - 49] : 0.0f);
-                    if (!ok) f[q] = 0.0f;
-                }
-                *reinterpret_cast<uint4 *>(smem + kOffSA + canon_off(tid, kc)) =
-                    make_uint4(pack_bf16(f[0], f[1]), pack_bf16(f[2], f[3]), pack_bf16(f[4], f[5]), pack_bf16(f[6], f[7]));
+            for (int kc = 0; kc < 4; ++kc) {
+                const int j = 8 * kc;
+                *reinterpret_cast<uint4 *>(sA(s) + canon_off(tid, 4 * half + kc)) =
+                    make_uint4(relu_bf16x2(h[j], h[j + 1]), relu_bf16x2(h[j + 2], h[j + 3]),
+                               relu_bf16x2(h[j + 4], h[j + 5]), relu_bf16x2(h[j + 6], h[j + 7]));
             }
         }
-        // layer 1: the A tile and the weights to the tensor core
         async_proxy_fence();
         tc_before_sync();
         __syncthreads();
         if (tid == 0) {
             tc_after_sync();
-            mma_layer(tmem, sbase + kOffSA, sbase + kOffSW1, bar_a);
-        }
-        bool ok = __all_sync(kFull, mbar_wait(bar_a, 0));
-        tc_after_sync();
-        // h1 = bf16(relu(acc + b1)) is layer 2's A tile, in place of x
-#pragma unroll
-        for (int half = 0; half < 2 && ok; ++half) {
-            float h[32];
-            tmem_row32(lane_base + 32 * half, h);
-#pragma unroll
-            for (int kc = 0; kc < 4; ++kc) {
-                uint32_t w[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int i = 8 * kc + 2 * q, n = 32 * half + i;
-                    w[q] = pack_bf16(fmaxf(h[i] + sB1[n], 0.0f), fmaxf(h[i + 1] + sB1[n + 1], 0.0f));
-                }
-                *reinterpret_cast<uint4 *>(smem + kOffSA + canon_off(tid, 4 * half + kc)) =
-                    make_uint4(w[0], w[1], w[2], w[3]);
+            mma_layer(tmem + 64 * s, sbase + kOffSA + s * kASize, sbase + kOffSW2, bar2, sbase + kOffSBA,
+                      sbase + kOffSBB);
+            ++issued2;
+            if (has_next) {
+                mma_layer(tmem + 64 * (s ^ 1), sbase + kOffSA + (s ^ 1) * kASize, sbase + kOffSW1, bar1);
+                ++issued1;
             }
+            ok = mbar_wait(bar2, (uint32_t)(done2 & 1));
+            done2 += ok;
         }
-        async_proxy_fence();
-        tc_before_sync();
         if (__syncthreads_or(!ok)) {
-            failed_tile = tile;
-            failed_parity = 0;
+            fail_from = t;
             break;
         }
-        if (tid == 0) {
-            tc_after_sync();
-            mma_layer(tmem, sbase + kOffSA, sbase + kOffSW2, bar_a);
-        }
-        ok = __all_sync(kFull, mbar_wait(bar_a, 1));
-        pending = !ok;
-        last_tile = tile;
         tc_after_sync();
-        if (ok) {
-            float o = 0.0f;
+        {
+            // w_px = sigmoid(w3 . relu(h2) + b3), h2 = acc (b2 added by the product)
+            float2 acc = make_float2(0.0f, 0.0f);
 #pragma unroll
             for (int half = 0; half < 2; ++half) {
                 float h[32];
-                tmem_row32(lane_base + 32 * half, h);
+                tmem_row32(tmem + lane_off + 64 * s + 32 * half, h);
 #pragma unroll
-                for (int i = 0; i < 32; ++i) o += sW3[32 * half + i] * fmaxf(h[i] + sB2[32 * half + i], 0.0f);
+                for (int j = 0; j < 32; j += 4) {
+                    const float4 w = *reinterpret_cast<const float4 *>(sW3 + 32 * half + j);
+                    acc = __ffma2_rn(make_float2(w.x, w.y), make_float2(fmaxf(h[j], 0.0f), fmaxf(h[j + 1], 0.0f)), acc);
+                    acc = __ffma2_rn(make_float2(w.z, w.w), make_float2(fmaxf(h[j + 2], 0.0f), fmaxf(h[j + 3], 0.0f)),
+                                     acc);
+                }
             }
-            o += sB3[0];
-            if (u < in.W && v < in.H) wpx[(size_t)v * in.W + u] = sValid[tid] ? 1.0f / (1.0f + expf(-o)) : 0.0f;
+            const float o = acc.x + acc.y + sW3[NH];
+            const int u = u0 + (tid & (kTW - 1)), v = v0 + tid / kTW;
+            if (u < in.W && v < in.H) wpx[(size_t)v * in.W + u] = sValid(s)[tid] ? 1.0f / (1.0f + expf(-o)) : 0.0f;
         }
-        tc_before_sync();  // this tile's TMEM reads come before the next tile's products
+        tc_before_sync();  // this tile's TMEM reads come before later products into its slot
+        __syncthreads();
     }
-    if (failed_tile < 0 && __syncthreads_or(pending)) {
-        failed_tile = last_tile;
-        failed_parity = 1;
-    }
-    if (failed_tile >= 0) {
-        // a product that never signalled completion: NaN weights for the
-        // CTA's remaining pixels (weighted integration skips them), one more
-        // bounded wait for the product in flight, then the TMEM is freed
-        for (int tile = failed_tile; tile < n_tiles; tile += gridDim.x) {
-            const int u = (tile % tiles_x) * kTW + (tid & (kTW - 1)), v = (tile / tiles_x) * kTH + tid / kTW;
+    if (fail_from >= 0) {
+        // NaN weights for the CTA's pixels from the failed tile on; one more
+        // bounded wait for each product still in flight
+        for (int t = fail_from; t < n_tiles; t += stride) {
+            const int u = (t % tiles_x) * kTW + (tid & (kTW - 1)), v = (t / tiles_x) * kTH + tid / kTW;
             if (u < in.W && v < in.H) wpx[(size_t)v * in.W + u] = __int_as_float(0x7fc00000);
         }
-        mbar_wait(bar_a, failed_parity);
+        if (tid == 0) {
+            for (; done1 < issued1; ++done1)
+                if (!mbar_wait(bar1, (uint32_t)(done1 & 1))) break;
+            for (; done2 < issued2; ++done2)
+                if (!mbar_wait(bar2, (uint32_t)(done2 & 1))) break;
+        }
     }
     tc_before_sync();
     __syncthreads();
@@ -593,6 +701,9 @@ int itm_conf_weights(const float *depth_dev, const itm_intrinsics *intr, float m
     if (reinterpret_cast<uintptr_t>(packed_dev) & 15) return ITM_ERR_ARG;
     const int tx = (intr->width + kTW - 1) / kTW, ty = (intr->height + kTH - 1) / kTH;
     const int n_tiles = tx * ty;
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(conf_weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kConfSmem);
+    if (attr != cudaSuccess) return check_cuda(attr);
     int grid = conf_grid();
     if (grid > n_tiles) grid = n_tiles;
     conf_weights_kernel<<<grid, 128, kConfSmem, (cudaStream_t)stream>>>(
