@@ -199,6 +199,43 @@ int itm_raycast_combined(itm_scene *const *scenes, const float *submap_from_worl
                          itm_stream stream);
 
 /* ---------------------------------------------------------------------
+ * One scene split over several processes (one per GPU) by slabs of block
+ * columns.  The paper has no counterpart: it is the multi-process form of
+ * the per-frame core of Sec. 4.2-4.4.  Block column x belongs to part
+ * floor(x / slab_blocks) mod parts.  A part allocates and integrates the
+ * blocks of its own columns and of one column on either side (every sample
+ * the raycast takes around a point of its own columns reads the same voxels
+ * as in the whole scene; those voxels are bit-identical to the whole
+ * scene's), so every process receives the whole depth frame and no data
+ * moves between processes until the raycast.  Each part's raycast reports
+ * only hits in its own columns; the parts' maps, gathered on every process,
+ * merge per pixel to the hit nearest to the camera (itm_raycast_merge).  The
+ * merged map is close to the whole scene's, not identical: a ray that
+ * reaches a part's columns from space the part does not hold starts its fine
+ * search there, so near slab boundaries a refined hit can move by a few mm.
+ */
+
+/* Make the scene part `index` of `parts` (1 <= parts, 0 <= index < parts,
+ * slab_blocks >= 2 block columns per slab); parts = 1 restores the whole
+ * scene.  Applies to later allocations and raycasts (blocks allocated before
+ * stay).  Host only.  Errors: ITM_ERR_ARG for invalid values. */
+int itm_scene_set_shard(itm_scene *scene, int parts, int index, int slab_blocks);
+
+/* Merge the raycasts of the parts of a split scene: vertex_parts_dev and
+ * normal_parts_dev hold `parts` maps of width x height float4, one part
+ * after another (as an all-gather leaves them); per pixel the hit (w = 1)
+ * with the smallest camera depth (row 2 of the world-to-camera transform,
+ * formed from T_wc as for itm_raycast, applied to the vertex with each
+ * operation rounded on its own) is copied to vertex_dev / normal_dev, equal
+ * depths going to the lower part; pixels with no hit get zeros.  All
+ * buffers are caller device memory, 16-byte aligned.  Asynchronous on
+ * `stream`.  Errors: ITM_ERR_ARG for null or unaligned buffers, parts < 1,
+ * invalid intrinsics or pose. */
+int itm_raycast_merge(const float *vertex_parts_dev, const float *normal_parts_dev, int parts,
+                      const itm_intrinsics *intr, const float T_wc[16], float *vertex_dev, float *normal_dev,
+                      itm_stream stream);
+
+/* ---------------------------------------------------------------------
  * Sec. 4.1.1 depth tracker (ITMDepthTracker): align a depth frame to the
  * vertex and normal maps of an itm_raycast by minimising the sum of squared
  * point-to-plane distances, over a resolution hierarchy of the depth image.

@@ -155,6 +155,9 @@ def _bind(lib):
     lib.orc_export_colour.argtypes = [P, i16p, u8p, I]
     lib.orc_threads.restype = I
     lib.orc_threads.argtypes = []
+    lib.orc_scene_set_shard.restype = I
+    lib.orc_scene_set_shard.argtypes = [P, I, I, I]
+    lib.orc_merge_raycasts.argtypes = [I, f32p, f32p, I, I, f32p, f32p, f32p]
     return lib
 
 
@@ -230,6 +233,13 @@ class Scene:
     @property
     def excess_used(self) -> int:
         return self._lib.orc_excess_used(self.p)
+
+    def set_shard(self, n, i, w):
+        """Make this scene part i of n: block column x belongs to part
+        floor(x / w) mod n; the part keeps its own columns and their x
+        neighbours, and its raycast reports only hits in its own columns."""
+        if self._lib.orc_scene_set_shard(self.p, int(n), int(i), int(w)) != 0:
+            raise ValueError("invalid shard")
 
     def export(self, with_voxels=True):
         """(coords int16 [n,3], sdf float32 [n,512], w float32 [n,512]) in
@@ -458,6 +468,24 @@ def track(depth, intr, iters, thresh, V, N, intr_r, T_ref, T_init):
     steps = _load().orc_track(d, W, H, _f32(intr), len(it), it, _f32(thresh), V.ravel(), N.ravel(), Wr, Hr,
                               _f32(intr_r), _f32(T_ref).ravel(), T)
     return T.reshape(4, 4), int(steps)
+
+
+def slab_owner(bx, n, w):
+    """Part that owns block column bx: floor(bx / w) mod n."""
+    return (int(bx) // int(w)) % int(n)
+
+
+def merge_raycasts(vtx, nrm, T_wc):
+    """The parts' raycasts (vtx, nrm: float32 [n, H, W, 4]) merged per pixel:
+    the hit nearest to the camera (camera depth from float(T_wc^-1)), equal
+    depths to the lower part."""
+    vtx = _f32(vtx)
+    nrm = _f32(nrm)
+    n, H, W = vtx.shape[:3]
+    vo = np.zeros((H, W, 4), dtype=np.float32)
+    no = np.zeros((H, W, 4), dtype=np.float32)
+    _load().orc_merge_raycasts(n, vtx.ravel(), nrm.ravel(), W, H, _f32(T_wc).ravel(), vo, no)
+    return vo, no
 
 
 def cell_triangles(F):

@@ -105,6 +105,9 @@ typedef struct {
     float **host;         /* per entry: the host slot (512 sdf then 512 weights), made on first use */
     long long swapped_in, swapped_out;
     uint8_t *rgbw;        /* colour voxels (orc_colour_enable): nv * 512 * {r, g, b, colour weight} */
+    /* one part of a scene split over shard_n processes by slabs of shard_w
+     * blocks along x (orc_scene_set_shard); shard_n <= 1: the whole scene */
+    int shard_n, shard_i, shard_w;
 } orc_scene;
 
 enum {
@@ -315,8 +318,54 @@ typedef struct {
     int status;
 } block_list;
 
+/* ------------------------------------------------------ slab partition
+ *
+ * A scene split over n parts (not in the paper; the multi-process form of
+ * the per-frame core): block column x belongs to part floor(x / w) mod n.
+ * Part i keeps the blocks of its own columns and of the ORC_SHARD_GHOST
+ * columns on either side, so that every trilinear sample, refinement step and
+ * normal of a point in its own columns reads the same voxels as the whole
+ * scene (each kept block's voxels equal the whole scene's bit for bit); its
+ * raycast reports only hits whose block is its own, and the parts' maps are
+ * merged per pixel by the hit nearest to the camera.  The merged map is close
+ * to the whole scene's but not the same computation: a ray that reaches a
+ * part's columns from space the part does not hold starts its fine search
+ * there, so near the slab boundaries its refined hit can differ by a few mm
+ * (and rarely hit or miss differently). */
+static int slab_owner(int bx, int n, int w)
+{
+    int q = bx >= 0 ? bx / w : -((-bx + w - 1) / w); /* floor(bx / w) */
+    int r = q % n;
+    return r < 0 ? r + n : r;
+}
+
+#define ORC_SHARD_GHOST 1
+
+static int shard_keeps(const orc_scene *s, int bx)
+{
+    if (s->shard_n <= 1) return 1;
+    for (int d = -ORC_SHARD_GHOST; d <= ORC_SHARD_GHOST; ++d)
+        if (slab_owner(bx + d, s->shard_n, s->shard_w) == s->shard_i) return 1;
+    return 0;
+}
+
+static int shard_owns(const orc_scene *s, int bx)
+{
+    return s->shard_n <= 1 || slab_owner(bx, s->shard_n, s->shard_w) == s->shard_i;
+}
+
+int orc_scene_set_shard(orc_scene *s, int n, int i, int w)
+{
+    if (n < 1 || i < 0 || i >= n || w < 2) return -1;
+    s->shard_n = n;
+    s->shard_i = i;
+    s->shard_w = w;
+    return 0;
+}
+
 static void emit_block(orc_scene *s, block_list *out, int bx, int by, int bz)
 {
+    if (!shard_keeps(s, bx)) return;
     if (!out) {
         insert_if_missing(s, bx, by, bz);
         return;
@@ -782,6 +831,7 @@ int orc_raycast(const orc_scene *s, int W, int H, const float intr[4], const flo
                 q[i] = p[i] * inv_s;
             }
             if (!(coord_ok(q[0]) && coord_ok(q[1]) && coord_ok(q[2]))) continue;
+            if (!shard_owns(s, ((int)floorf(q[0] + 0.5f)) >> 3)) continue; /* another part's hit */
             vtx[o4] = p[0];
             vtx[o4 + 1] = p[1];
             vtx[o4 + 2] = p[2];
@@ -807,6 +857,35 @@ int orc_raycast(const orc_scene *s, int W, int H, const float intr[4], const flo
         }
     }
     return hits;
+}
+
+/* The parts' raycasts (n maps of W x H float4 vertices and normals, one part
+ * after another) merged: per pixel the hit nearest to the camera, its camera
+ * depth z = row 2 of float(T_wc^-1) applied to the vertex; equal depths go to
+ * the lower part.  No hit in any part: zeros. */
+void orc_merge_raycasts(int n, const float *vtx, const float *nrm, int W, int H, const float T_wc[16],
+                        float *vtx_out, float *nrm_out)
+{
+    float M[16];
+    rigid_inverse(T_wc, M);
+    const size_t np = (size_t)W * H;
+    for (size_t o = 0; o < np; ++o) {
+        int best = -1;
+        float best_z = 0.0f;
+        for (int k = 0; k < n; ++k) {
+            const float *V = vtx + 4 * ((size_t)k * np + o);
+            if (!(V[3] > 0.0f)) continue;
+            const float z = row_apply(&M[8], V[0], V[1], V[2]);
+            if (best < 0 || z < best_z) {
+                best = k;
+                best_z = z;
+            }
+        }
+        for (int c = 0; c < 4; ++c) {
+            vtx_out[4 * o + c] = best < 0 ? 0.0f : vtx[4 * ((size_t)best * np + o) + c];
+            nrm_out[4 * o + c] = best < 0 ? 0.0f : nrm[4 * ((size_t)best * np + o) + c];
+        }
+    }
 }
 
 /* ------------------------------------------------------------ combined map */

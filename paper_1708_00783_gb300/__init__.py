@@ -126,6 +126,8 @@ def _load():
         "itm_depth_halve": (I, [P, I, I, P, P]),
         "itm_mesh": (I, [P, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), P]),
         "itm_mesh_case_table": (I, [P, P]),
+        "itm_scene_set_shard": (I, [P, I, I, I]),
+        "itm_raycast_merge": (I, [P, P, I, ip, fp16, P, P, P]),
         "itm_icp_reduce": (I, [P, ip, fp16, P, P, ip, fp16, F, P, P]),
         "itm_icp_step": (I, [ctypes.POINTER(ctypes.c_double), fp16, ctypes.POINTER(ctypes.c_double)]),
         "itm_track_scratch_bytes": (ctypes.c_size_t, [I, I, I]),
@@ -338,6 +340,25 @@ def itm_mesh(scene, triangles=None, capacity=0, stream=None):
         return n.value
     _check(r, "itm_mesh")
     return n.value
+
+
+def itm_scene_set_shard(scene, parts, index, slab_blocks):
+    """Make the scene part `index` of `parts` of a scene split by slabs of
+    `slab_blocks` block columns (parts = 1: the whole scene)."""
+    _check(_lib.itm_scene_set_shard(scene, int(parts), int(index), int(slab_blocks)), "itm_scene_set_shard")
+
+
+def itm_raycast_merge(vertex_parts, normal_parts, parts, intr, T_wc, vertex, normal, stream=None):
+    """Per pixel, the parts' hit nearest to the camera (device float4 maps:
+    parts x height x width in, height x width out)."""
+    n = _pixels(intr)
+    _buffer(vertex_parts, _f32_t(), 4 * n * int(parts), "itm_raycast_merge: vertex_parts")
+    _buffer(normal_parts, _f32_t(), 4 * n * int(parts), "itm_raycast_merge: normal_parts")
+    _buffer(vertex, _f32_t(), 4 * n, "itm_raycast_merge: vertex")
+    _buffer(normal, _f32_t(), 4 * n, "itm_raycast_merge: normal")
+    a, p = _pose(T_wc)
+    _check(_lib.itm_raycast_merge(_ptr(vertex_parts), _ptr(normal_parts), int(parts), ctypes.byref(intr), p,
+                                  _ptr(vertex), _ptr(normal), _stream(stream)), "itm_raycast_merge")
 
 
 def itm_mesh_case_table():
@@ -657,6 +678,10 @@ class Scene:
             self.close()
         except Exception:
             pass
+
+    def set_shard(self, parts, index, slab_blocks):
+        """Make this scene part `index` of `parts` (see itm_scene_set_shard)."""
+        itm_scene_set_shard(self.handle, parts, index, slab_blocks)
 
     def reset(self, stream=None):
         itm_scene_reset(self.handle, stream)

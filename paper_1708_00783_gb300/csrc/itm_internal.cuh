@@ -109,6 +109,9 @@ struct SceneDev {
     float voxel_size, mu, z_min, z_max;
     float inv_mu;  // RN(1 / mu)
     int max_w, weight_mode;
+    // one part of a scene split by slabs of block columns (itm_scene_set_shard);
+    // shard_n <= 1: the whole scene
+    int shard_n, shard_i, shard_w;
 };
 
 struct Intr {
@@ -193,6 +196,34 @@ __device__ __forceinline__ int lookup_cg(const SceneDev &s, int bx, int by, int 
         idx = s.nb + e.z - 1;
     }
     return -1;
+}
+
+// ------------------------------------------------------ slab partition
+// Block column x belongs to part floor(x / w) mod n; a part keeps its own
+// columns and kShardGhost columns on either side (whose voxels every sample
+// around a point of its own columns reads), and reports only raycast hits in
+// its own columns.
+constexpr int kShardGhost = 1;
+
+__host__ __device__ __forceinline__ int slab_owner(int bx, int n, int w)
+{
+    const int q = bx >= 0 ? bx / w : -((-bx + w - 1) / w);  // floor(bx / w)
+    const int r = q % n;
+    return r < 0 ? r + n : r;
+}
+
+__device__ __forceinline__ bool shard_keeps(const SceneDev &s, int bx)
+{
+    if (s.shard_n <= 1) return true;
+    bool keep = false;
+#pragma unroll
+    for (int d = -kShardGhost; d <= kShardGhost; ++d) keep = keep || slab_owner(bx + d, s.shard_n, s.shard_w) == s.shard_i;
+    return keep;
+}
+
+__device__ __forceinline__ bool shard_owns(const SceneDev &s, int bx)
+{
+    return s.shard_n <= 1 || slab_owner(bx, s.shard_n, s.shard_w) == s.shard_i;
 }
 
 // ------------------------------------------------ IEEE round-to-nearest ops
@@ -294,5 +325,7 @@ cudaError_t launch_track(const float *depth, const Intr &in0, int levels, const 
 cudaError_t launch_raycast_combined(const SceneDev *subs, const Mat34 *P, int n, const Intr &in, const Mat34 &T_wc,
                                     float4 *vtx, float4 *nrm, cudaStream_t st);
 cudaError_t launch_depth_u16(const uint16_t *raw, float *out, int64_t n, cudaStream_t st);
+cudaError_t launch_raycast_merge(const float4 *vtx, const float4 *nrm, int parts, long long npix, const Mat34 &M_d,
+                                 float4 *vo, float4 *no, cudaStream_t st);
 cudaError_t launch_reset(const SceneDev &s, cudaStream_t st);
 }  // namespace itm

@@ -221,4 +221,39 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
     return cudaGetLastError();
 }
 
+// Parts' raycasts of a split scene merged per pixel: the hit nearest to the
+// camera (camera depth = row 2 of M_d applied to the vertex, each operation
+// rounded on its own), equal depths to the lower part; no hit: zeros.
+__global__ void __launch_bounds__(256) merge_kernel(const float4 *__restrict__ vtx, const float4 *__restrict__ nrm,
+                                                    int parts, long long npix, Mat34 M, float4 *__restrict__ vo,
+                                                    float4 *__restrict__ no)
+{
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < npix;
+         o += (long long)gridDim.x * blockDim.x) {
+        int best = -1;
+        float best_z = 0.0f;
+        for (int k = 0; k < parts; ++k) {
+            const float4 V = __ldg(&vtx[(size_t)k * npix + o]);
+            if (!(V.w > 0.0f)) continue;
+            const float z = row_apply(&M.m[8], V.x, V.y, V.z);
+            if (best < 0 || z < best_z) {
+                best = k;
+                best_z = z;
+            }
+        }
+        const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+        vo[o] = best < 0 ? zero : __ldg(&vtx[(size_t)best * npix + o]);
+        no[o] = best < 0 ? zero : __ldg(&nrm[(size_t)best * npix + o]);
+    }
+}
+
+cudaError_t launch_raycast_merge(const float4 *vtx, const float4 *nrm, int parts, long long npix, const Mat34 &M_d,
+                                 float4 *vo, float4 *no, cudaStream_t st)
+{
+    if (npix <= 0) return cudaSuccess;
+    const long long blocks = (npix + 255) / 256;
+    merge_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, st>>>(vtx, nrm, parts, npix, M_d, vo, no);
+    return cudaGetLastError();
+}
+
 }  // namespace itm

@@ -288,6 +288,36 @@ int itm_raycast(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16],
     return r;
 }
 
+int itm_scene_set_shard(itm_scene *sc, int parts, int index, int slab_blocks)
+{
+    if (!sc || parts < 1 || index < 0 || index >= parts || slab_blocks < 2) return ITM_ERR_ARG;
+    sc->d.shard_n = parts;
+    sc->d.shard_i = index;
+    sc->d.shard_w = slab_blocks;
+    sc->alloc_epoch += 1;  // the raycast's search ranges are computed again
+    return ITM_OK;
+}
+
+int itm_raycast_merge(const float *vertex_parts_dev, const float *normal_parts_dev, int parts,
+                      const itm_intrinsics *intr, const float T_wc[16], float *vertex_dev, float *normal_dev,
+                      itm_stream stream)
+{
+    Range range_("itm_raycast_merge");
+    if (!vertex_parts_dev || !normal_parts_dev || parts < 1 || !valid_intr(intr) || !valid_pose(T_wc) ||
+        !vertex_dev || !normal_dev)
+        return ITM_ERR_ARG;
+    const uintptr_t al = reinterpret_cast<uintptr_t>(vertex_parts_dev) | reinterpret_cast<uintptr_t>(normal_parts_dev) |
+                         reinterpret_cast<uintptr_t>(vertex_dev) | reinterpret_cast<uintptr_t>(normal_dev);
+    if (al & 15) return ITM_ERR_ARG;
+    Mat34 M;
+    rigid_inverse_rows(T_wc, M);
+    return check_cuda(launch_raycast_merge(reinterpret_cast<const float4 *>(vertex_parts_dev),
+                                           reinterpret_cast<const float4 *>(normal_parts_dev), parts,
+                                           (long long)intr->width * intr->height, M,
+                                           reinterpret_cast<float4 *>(vertex_dev),
+                                           reinterpret_cast<float4 *>(normal_dev), (cudaStream_t)stream));
+}
+
 int itm_raycast_range(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16], float *zmin_dev,
                       float *zmax_dev, itm_stream stream)
 {
