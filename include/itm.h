@@ -486,6 +486,17 @@ int itm_batch_run(itm_batch *batch, const itm_batch_item *items, int n, itm_stre
  * sizes in use. */
 int itm_batch_set_tuning(itm_batch *batch, const int *ctas_per_sm, int n);
 int itm_batch_get_tuning(itm_batch *batch, int *grid_ctas, int n);
+
+/* The batch's schedule, ITM_BATCH_KNOBS values: [0] blocks one integration
+ * CTA updates at once (1, 2 or 4; 64 threads each), [1] and [2] the
+ * enumeration's and the raycast's walk over the virtual 32x8-pixel tiles of
+ * all items (0: in item order; 1: scattered, tile v taken as v * P mod the
+ * tile count for a P coprime to it, interleaving the items).  Results do not
+ * depend on the schedule.  Drops the captured graph.  Default [1, 0, 0].
+ * Errors: ITM_ERR_ARG for another count or value. */
+#define ITM_BATCH_KNOBS 3
+int itm_batch_set_schedule(itm_batch *batch, const int *knobs, int n);
+int itm_batch_get_schedule(itm_batch *batch, int *knobs, int n);
 int itm_batch_set_graph(itm_batch *batch, int use_graph);
 
 /* Library version string. */

@@ -33,6 +33,7 @@ ITM_NOALLOC_OVERFLOW = -(1 << 31)  # count bit 31 (a negative count): the fixed 
 ITM_MLP_FEATURES, ITM_MLP_HIDDEN, ITM_MLP_PARAMS = 52, 64, 7617
 ITM_MLP_PACKED_BYTES, ITM_MLP_SCRATCH_PER_SAMPLE = 17168, 257
 ITM_BATCH_STAGES = 6
+ITM_BATCH_KNOBS = 3
 ITM_COMBINED_MAX = 16
 ITM_ICP_SUMS = 29
 ITM_ICP_WORK_DOUBLES = ITM_ICP_SUMS * 1025
@@ -88,6 +89,7 @@ EXPORTED = [
     "itm_scene_import", "itm_hash_index", "itm_version", "itm_frame_blocks_noalloc", "itm_raycast_range",
     "itm_mlp_pack", "itm_conf_weights", "itm_conf_features", "itm_mlp_loss_grad", "itm_mlp_adam",
     "itm_batch_create", "itm_batch_destroy", "itm_batch_run", "itm_batch_set_tuning", "itm_batch_get_tuning",
+    "itm_batch_set_schedule", "itm_batch_get_schedule",
     "itm_batch_set_graph", "itm_swap_enable", "itm_swap_in", "itm_swap_out", "itm_swap_get_counters",
     "itm_swap_export_host", "itm_colour_enable", "itm_integrate_colour", "itm_colour_at", "itm_scene_export_colour",
 ]
@@ -142,6 +144,8 @@ def _load():
         "itm_batch_run": (I, [P, ctypes.POINTER(itm_batch_item), I, P]),
         "itm_batch_set_tuning": (I, [P, ctypes.POINTER(I), I]),
         "itm_batch_get_tuning": (I, [P, ctypes.POINTER(I), I]),
+        "itm_batch_set_schedule": (I, [P, ctypes.POINTER(I), I]),
+        "itm_batch_get_schedule": (I, [P, ctypes.POINTER(I), I]),
         "itm_batch_set_graph": (I, [P, I]),
         "itm_swap_enable": (I, [P, I, I]),
         "itm_swap_in": (I, [P, P]),
@@ -564,6 +568,19 @@ def itm_batch_run(batch, items, stream=None):
 def itm_batch_set_tuning(batch, ctas_per_sm):
     a = (ctypes.c_int * ITM_BATCH_STAGES)(*[int(x) for x in ctas_per_sm])
     _check(_lib.itm_batch_set_tuning(batch, a, ITM_BATCH_STAGES), "itm_batch_set_tuning")
+
+
+def itm_batch_set_schedule(batch, knobs):
+    """[blocks per integration CTA (1, 2, 4), scattered enumeration walk (0/1),
+    scattered raycast walk (0/1)]."""
+    a = (ctypes.c_int * ITM_BATCH_KNOBS)(*[int(x) for x in knobs])
+    _check(_lib.itm_batch_set_schedule(batch, a, ITM_BATCH_KNOBS), "itm_batch_set_schedule")
+
+
+def itm_batch_get_schedule(batch):
+    a = (ctypes.c_int * ITM_BATCH_KNOBS)()
+    _check(_lib.itm_batch_get_schedule(batch, a, ITM_BATCH_KNOBS), "itm_batch_get_schedule")
+    return list(a)
 
 
 def itm_batch_get_tuning(batch):

@@ -17,7 +17,12 @@
 // launches the graph.
 //
 // Launch shapes are tunable per stage (CTAs per SM; itm_batch_set_tuning),
-// which is what the autotuner in paper_1708_00783_gb300/autotune.py searches.
+// and so is the schedule (itm_batch_set_schedule): the number of blocks an
+// integration CTA updates at once (64 threads per block), and whether the
+// enumeration and raycast CTAs walk the virtual 32x8 tiles in order or
+// scattered (tile v taken as v * P mod total with P coprime to the total, so
+// the items' tiles, whose costs differ by item, interleave over the grid).
+// The autotuner in paper_1708_00783_gb300/autotune.py searches both.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -47,8 +52,19 @@ struct ItemDev {
 };
 
 struct BatchHead {
-    int n, cta_total, pad0, pad1;
+    int n, cta_total;
+    int scatter_p;  // multiplier of the scattered tile order (coprime to cta_total)
+    int pad;
 };
+
+// knobs of itm_batch_set_schedule
+enum Knob { K_INTEG_BLOCKS = 0, K_ENUM_SCATTER, K_RAY_SCATTER, K_COUNT };
+
+// virtual tile v in the walk order of a stage: in order, or scattered
+__device__ __forceinline__ int walk_tile(int v, int total, int p, bool scatter)
+{
+    return scatter ? (int)(((long long)v * p) % total) : v;
+}
 
 // last index i in [0, n) with prefix[i] <= v (prefix ascending, prefix[0] = 0)
 __device__ __forceinline__ int find_item(const int *prefix, int n, int v)
@@ -90,13 +106,15 @@ __global__ void __launch_bounds__(256) batch_begin_kernel(const ItemDev *__restr
     }
 }
 
-__global__ void __launch_bounds__(256) batch_enumerate_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
+__global__ void __launch_bounds__(256) batch_enumerate_kernel(const ItemDev *__restrict__ items, const BatchHead *head,
+                                                                bool scatter)
 {
     __shared__ int begin[kMaxItems + 1];
-    const int n = head->n, total = head->cta_total;
+    const int n = head->n, total = head->cta_total, p = head->scatter_p;
     for (int i = threadIdx.x; i < n; i += blockDim.x) begin[i] = items[i].cta_begin;
     __syncthreads();
-    for (int vt = blockIdx.x; vt < total; vt += gridDim.x) {
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+        const int vt = walk_tile(v, total, p, scatter);
         const int k = find_item(begin, n, vt);
         const ItemDev &it = items[k];
         const int local = vt - begin[k];
@@ -143,8 +161,8 @@ __global__ void __launch_bounds__(256) batch_visible_kernel(const ItemDev *__res
     }
 }
 
-__global__ void __launch_bounds__(64) batch_integrate_kernel(const ItemDev *__restrict__ items, const BatchHead *head,
-                                                             float2 nz)
+__global__ void __launch_bounds__(256) batch_integrate_kernel(const ItemDev *__restrict__ items, const BatchHead *head,
+                                                              float2 nz)
 {
     __shared__ int prefix[kMaxItems + 1];
     __shared__ float2 rcp_w[256];
@@ -159,8 +177,9 @@ __global__ void __launch_bounds__(64) batch_integrate_kernel(const ItemDev *__re
             atomicAdd(&items[k].s.ctr->frames, 1ull);
         }
     }
-    const int t = threadIdx.x;
-    for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    // blockDim.x / 64 blocks at once, 64 threads each
+    const int t = threadIdx.x & 63, per = blockDim.x >> 6;
+    for (int vb = blockIdx.x * per + (threadIdx.x >> 6); vb < total; vb += gridDim.x * per) {
         const int k = find_item(prefix, n, vb);
         const ItemDev &it = items[k];
         const int ptr = __ldg(&it.s.visible[vb - prefix[k]]);
@@ -199,13 +218,15 @@ __global__ void __launch_bounds__(256) batch_range_kernel(const ItemDev *__restr
     }
 }
 
-__global__ void __launch_bounds__(256, 4) batch_raycast_kernel(const ItemDev *__restrict__ items, const BatchHead *head)
+__global__ void __launch_bounds__(256, 4) batch_raycast_kernel(const ItemDev *__restrict__ items, const BatchHead *head,
+                                                                   bool scatter)
 {
     __shared__ int begin[kMaxItems + 1];
-    const int n = head->n, total = head->cta_total;
+    const int n = head->n, total = head->cta_total, p = head->scatter_p;
     for (int i = threadIdx.x; i < n; i += blockDim.x) begin[i] = items[i].cta_begin;
     __syncthreads();
-    for (int vt = blockIdx.x; vt < total; vt += gridDim.x) {
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+        const int vt = walk_tile(v, total, p, scatter);
         const int k = find_item(begin, n, vt);
         const ItemDev &it = items[k];
         if (!it.raycast) continue;
@@ -246,21 +267,47 @@ struct itm_batch {
     int sms;
     int per_sm[ST_COUNT];  // 0: as many as fit
     int grid[ST_COUNT];
+    int knob[K_COUNT];     // itm_batch_set_schedule
     int use_graph;
     cudaGraph_t graph;
     cudaGraphExec_t exec;
     int have_graph;
 };
 
+static int stage_threads(const itm_batch *b, int st)
+{
+    return st == ST_INTEGRATE ? 64 * b->knob[K_INTEG_BLOCKS] : kStageThreads[st];
+}
+
 static void batch_grids(itm_batch *b)
 {
     for (int st = 0; st < ST_COUNT; ++st) {
         int fit = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, stage_kernel(st), kStageThreads[st], 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, stage_kernel(st), stage_threads(b, st), 0);
         if (fit < 1) fit = 1;
         int per = b->per_sm[st] > 0 && b->per_sm[st] < fit ? b->per_sm[st] : fit;
         b->grid[st] = b->sms * per;
     }
+}
+
+static int gcd(int a, int b)
+{
+    while (b) {
+        const int t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// a multiplier coprime to total near 0.618 total (consecutive tiles land far
+// apart in the scattered order); 1 for total <= 2
+static int scatter_multiplier(int total)
+{
+    if (total <= 2) return 1;
+    for (int p = (int)(0.6180339887 * total); p > 1; --p)
+        if (gcd(p, total) == 1) return p;
+    return 1;
 }
 
 static void drop_graph(itm_batch *b)
@@ -277,13 +324,14 @@ static cudaError_t launch_stages(itm_batch *b, cudaStream_t st)
     const ItemDev *it = b->d_items;
     const BatchHead *h = b->d_head;
     batch_begin_kernel<<<b->max_items, 256, 0, st>>>(it, h);
-    batch_enumerate_kernel<<<b->grid[ST_ENUM], 256, 0, st>>>(it, h);
+    batch_enumerate_kernel<<<b->grid[ST_ENUM], 256, 0, st>>>(it, h, b->knob[K_ENUM_SCATTER] != 0);
     batch_commit_kernel<<<b->grid[ST_COMMIT], 256, 0, st>>>(it, h);
     batch_overflow_kernel<<<b->max_items, kOvfThreads, 0, st>>>(it, h);
     batch_visible_kernel<<<b->grid[ST_VISIBLE], 256, 0, st>>>(it, h);
-    batch_integrate_kernel<<<b->grid[ST_INTEGRATE], 64, 0, st>>>(it, h, make_float2(-0.0f, -0.0f));
+    batch_integrate_kernel<<<b->grid[ST_INTEGRATE], stage_threads(b, ST_INTEGRATE), 0, st>>>(it, h,
+                                                                                        make_float2(-0.0f, -0.0f));
     batch_range_kernel<<<b->grid[ST_RANGE], 256, 0, st>>>(it, h);
-    batch_raycast_kernel<<<b->grid[ST_RAYCAST], 256, 0, st>>>(it, h);
+    batch_raycast_kernel<<<b->grid[ST_RAYCAST], 256, 0, st>>>(it, h, b->knob[K_RAY_SCATTER] != 0);
     return cudaGetLastError();
 }
 
@@ -297,6 +345,7 @@ int itm_batch_create(int max_items, itm_batch **out)
     if (!b) return ITM_ERR_ARG;
     b->max_items = max_items;
     b->use_graph = 1;
+    b->knob[K_INTEG_BLOCKS] = 1;
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
@@ -357,6 +406,26 @@ int itm_batch_get_tuning(itm_batch *b, int *grid_ctas, int n)
 {
     if (!b || !grid_ctas || n != ST_COUNT) return ITM_ERR_ARG;
     for (int i = 0; i < n; ++i) grid_ctas[i] = b->grid[i];
+    return ITM_OK;
+}
+
+int itm_batch_set_schedule(itm_batch *b, const int *knobs, int n)
+{
+    if (!b || !knobs || n != K_COUNT) return ITM_ERR_ARG;
+    const int kb = knobs[K_INTEG_BLOCKS];
+    if (!(kb == 1 || kb == 2 || kb == 4)) return ITM_ERR_ARG;
+    if ((knobs[K_ENUM_SCATTER] & ~1) || (knobs[K_RAY_SCATTER] & ~1)) return ITM_ERR_ARG;
+    cudaDeviceSynchronize();
+    for (int i = 0; i < n; ++i) b->knob[i] = knobs[i];
+    batch_grids(b);
+    drop_graph(b);
+    return ITM_OK;
+}
+
+int itm_batch_get_schedule(itm_batch *b, int *knobs, int n)
+{
+    if (!b || !knobs || n != K_COUNT) return ITM_ERR_ARG;
+    for (int i = 0; i < n; ++i) knobs[i] = b->knob[i];
     return ITM_OK;
 }
 
@@ -425,7 +494,8 @@ int itm_batch_run(itm_batch *b, const itm_batch_item *items, int n, itm_stream s
     }
     h->n = n;
     h->cta_total = cta_total;
-    h->pad0 = h->pad1 = 0;
+    h->scatter_p = scatter_multiplier(cta_total);
+    h->pad = 0;
     cudaError_t e = cudaMemcpyAsync(b->d_head, h, sizeof(BatchHead) + sizeof(ItemDev) * (size_t)n,
                                     cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(b->ev[slot], st);

@@ -75,12 +75,17 @@ def as_intr(itm, c):
     return itm.make_intrinsics(c.width, c.height, c.fx, c.fy, c.cx, c.cy)
 
 
-@pytest.mark.parametrize("use_graph", [True, False])
-def test_batch_equals_single_scene_path(itm, use_graph):
+@pytest.mark.parametrize("use_graph,schedule", [(True, [1, 0, 0]), (False, [1, 0, 0]), (True, [4, 1, 1]),
+                                                 (True, [2, 0, 1])])
+def test_batch_equals_single_scene_path(itm, use_graph, schedule):
+    """Also with the schedule knobs moved (blocks per integration CTA,
+    scattered tile walks): results do not depend on them."""
     import torch
     specs = scene_specs()
     batch = itm.itm_batch_create(8)
     itm.itm_batch_set_graph(batch, use_graph)
+    itm.itm_batch_set_schedule(batch, schedule)
+    assert itm.itm_batch_get_schedule(batch) == schedule
     batched = [itm.Scene(**p) for _, p, _ in specs]
     alone = [itm.Scene(**p) for _, p, _ in specs]
     orcs = [oracle_scene(p) for _, p, _ in specs]
@@ -204,6 +209,12 @@ def test_batch_rejects_invalid_items(itm):
     c = itm.Scene(**w.params)
     with pytest.raises(itm.ItmError):
         itm.itm_batch_run(batch, [(s.handle, D, ci, f.T_wc, None, None) for s in (a, b, c)])  # over capacity
+    for knobs in ([3, 0, 0], [1, 2, 0], [1, 0, -1], [1, 0]):
+        with pytest.raises(itm.ItmError):
+            if len(knobs) == 3:
+                itm.itm_batch_set_schedule(batch, knobs)
+            else:
+                itm._check(itm._lib.itm_batch_set_schedule(batch, (itm.ctypes.c_int * 2)(*knobs), 2), "x")
     bad = f.T_wc.copy()
     bad[0, 0] = np.nan
     with pytest.raises(itm.ItmError):
