@@ -267,18 +267,33 @@ def write_frames_jsonl(path, frames, stage):
             f.write(json.dumps(dict({"frame": int(k)}, **{n: float(v) for n, v in zip(names, row)})) + "\n")
 
 
+# Arm CPU part numbers (/proc/cpuinfo "CPU part", implementer 0x41) of the
+# server cores this may run on
+ARM_PARTS = {0xd0c: "Neoverse-N1", 0xd40: "Neoverse-V1", 0xd49: "Neoverse-N2", 0xd4f: "Neoverse-V2",
+             0xd8e: "Neoverse-N3", 0xd84: "Neoverse-V3"}
+
+
 def host_cpu():
-    """CPU model and logical core count of this host, for the CPU baseline."""
+    """CPU model and logical core count of this host, for the CPU baseline
+    (on Arm, the core from the CPU implementer and part numbers)."""
     import platform
     model = None
+    impl = part = None
     try:
         with open("/proc/cpuinfo") as f:
             for ln in f:
-                if ln.lower().startswith("model name"):
-                    model = ln.split(":", 1)[1].strip()
-                    break
-    except OSError:
+                key = ln.split(":", 1)[0].strip().lower()
+                val = ln.split(":", 1)[1].strip() if ":" in ln else ""
+                if key == "model name" and model is None:
+                    model = val
+                elif key == "cpu implementer" and impl is None:
+                    impl = int(val, 0)
+                elif key == "cpu part" and part is None:
+                    part = int(val, 0)
+    except (OSError, ValueError):
         pass
+    if model is None and impl == 0x41 and part is not None:
+        model = "Arm %s (CPU part %#x)" % (ARM_PARTS.get(part, "core"), part)
     return "%s (%s), %d logical cores" % (model or platform.processor() or "unknown CPU", platform.machine(),
                                           os.cpu_count() or 0)
 
@@ -621,6 +636,107 @@ def run_swap_section(itm, torch, stream, params, raw_dev, poses, ci, depth, vtx,
     }
 
 
+LARGE_FRAMES = list(range(0, 1000, 40))  # 25 frames along the whole corridor walk
+LARGE_WARMUP = 3
+LARGE_K = 1 << 17                         # blocks moved per swap call at most
+
+
+def _render_large(k):
+    from synth import large_workload
+    f = large_workload().frame(k)
+    return k, f.depth_u16, f.T_wc
+
+
+def render_large_frames(procs=None):
+    ctx = mp.get_context("spawn")
+    out = {}
+    with ctx.Pool(procs or min(os.cpu_count() or 1, 32)) as pool:
+        for k, d, T in pool.imap_unordered(_render_large, LARGE_FRAMES):
+            out[k] = (d, T)
+    return out
+
+
+def run_large_section(itm, torch, dev, stream, frames, peak):
+    """The large configuration as stated: the 20x10x3 m corridor at 2 mm
+    voxels, mu 10 mm, 2^22 buckets (+ 2^20 excess entries) and at most 2^21
+    resident blocks, with Sec. 5 swapping keeping the resident set (blocks leave the
+    device after one allocation without a segment meeting them, at most
+    LARGE_K moves per call).  Frames 40 apart along the 1000-frame walk, so the
+    map grows to about two million blocks.  Per frame: allocation from the
+    millimetre frame, swap-in, integration, raycast, swap-out, each timed with
+    CUDA events; L2 flushed between frames.  The integration roofline uses the
+    room's formula (10 B per updated voxel + 4 B per pixel + 12 B per visible
+    block)."""
+    from synth import large_workload
+    w = large_workload()
+    H, W = w.intr.height, w.intr.width
+    ci = itm.make_intrinsics(W, H, w.intr.fx, w.intr.fy, w.intr.cx, w.intr.cy)
+    # 2^20 excess entries: the walk's map (about 2.8 M blocks, swapped-out
+    # ones keep their entries) puts about 0.75 M keys outside their bucket
+    sc = itm.Scene(**dict(w.params, num_excess=1 << 20))
+    sc.swap_enable(LARGE_K, 1)
+    raw = {k: torch.from_numpy(frames[k][0].view(np.int16)).to(dev) for k in LARGE_FRAMES}
+    depth = torch.empty((H, W), dtype=torch.float32, device=dev)
+    vtx = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+    nrm = torch.empty_like(vtx)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def frame(k, e=None):
+        T = frames[k][1]
+        calls = (lambda: itm.itm_allocate_u16(sc.handle, raw[k], depth, ci, T, stream),
+                 lambda: sc.swap_in(stream),
+                 lambda: itm.itm_integrate(sc.handle, depth, ci, T, stream),
+                 lambda: itm.itm_raycast(sc.handle, ci, T, vtx, nrm, stream),
+                 lambda: sc.swap_out(stream))
+        for j, c in enumerate(calls):
+            if e is not None:
+                e[j].record(stream)
+            c()
+        if e is not None:
+            e[5].record(stream)
+
+    for k in LARGE_FRAMES[:LARGE_WARMUP]:
+        frame(k)
+    torch.cuda.synchronize()
+    st0, c0 = sc.stats(), sc.swap_counters()
+    timed = LARGE_FRAMES[LARGE_WARMUP:]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in timed]
+    for i, k in enumerate(timed):
+        frame(k, ev[i])
+        flush.zero_()
+    torch.cuda.synchronize()
+    st1, c1 = sc.stats(), sc.swap_counters()
+    stage = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(5)] for e in ev])
+    n = len(timed)
+    updated = st1["updated_voxels"] - st0["updated_voxels"]
+    visited = st1["visited_voxels"] - st0["visited_voxels"]
+    integ_ms = float(stage[:, 2].sum())
+    alg = 10.0 * updated + 4.0 * H * W * n + 12.0 * visited / 512.0
+    achieved = alg / (integ_ms / 1000.0) / 1e9
+    names = ["u16_to_f32_and_allocate", "swap_in", "integrate", "raycast", "swap_out"]
+    out = {
+        "workload": "corridor 20x10x3 m with 200 primitives, 640x480, 2 mm voxels, mu 10 mm, 2^22 buckets + 2^20 "
+                    "excess, 2^21 resident blocks with swapping (host store pinned and mapped into the device); "
+                    "frames %d..%d step 40 of the 1000-frame walk (first %d untimed)" % (
+                        LARGE_FRAMES[0], LARGE_FRAMES[-1], LARGE_WARMUP),
+        "status": st1["status"],
+        "frames_per_s": n / (float(stage.sum()) / 1000.0),
+        "stage_ms_mean": {nm: float(stage[:, j].mean()) for j, nm in enumerate(names)},
+        "voxel_updates_per_s": updated / (float(stage.sum()) / 1000.0),
+        "device_blocks_end": st1["allocated_blocks"],
+        "map_blocks_end": st1["allocated_blocks"] + c1["swapped_out"],
+        "blocks_in_per_frame": (c1["moved_in"] - c0["moved_in"]) / n,
+        "blocks_out_per_frame": (c1["moved_out"] - c0["moved_out"]) / n,
+        "visible_blocks_mean": visited / 512.0 / n,
+        "updated_voxels_per_frame": updated / n,
+        "integration_roofline": {"kernel": "integrate_kernel<0>", "bound": "hbm", "achieved": achieved,
+                                 "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                                 "algorithmic_bytes_per_launch": alg / n, "launch_ms_mean": integ_ms / n},
+    }
+    sc.close()
+    return out
+
+
 def run_colour_section(itm, torch, dev, stream, params, raw_dev, poses, ci, depth, vtx, nrm, flush, warmup):
     """Sec. 3.1 colour voxels on the room trajectory: per frame allocation,
     depth + colour integration of a 640x480 RGB frame (a colour camera 2 cm
@@ -846,6 +962,8 @@ def run_ours(args, world, rank, local):
         small_b = render_batched_frames(n_bsteps + 10)
     if extra and args.learned:
         conf_frames = render_learned_frames()
+    if extra and args.large:
+        large_frames = render_large_frames()
 
     import torch
     torch.cuda.set_device(local)
@@ -913,6 +1031,15 @@ def run_ours(args, world, rank, local):
     updated = st1["updated_voxels"] - st0["updated_voxels"]
     visited = st1["visited_voxels"] - st0["visited_voxels"]
     updated_all = sum_over_ranks(float(updated), world, dev)
+
+    # raycast: a lower bound on the unique bytes the last timed raycast read --
+    # every block holding a hit (its 512 x 5 B of sdf and weights, the samples
+    # around the hit read from it) and its hash entry (16 B)
+    vh = vtx.cpu().numpy()
+    hit = vh[..., 3] > 0
+    g = np.floor(vh[hit][:, :3].astype(np.float64) / w.params["voxel_size"] + 0.5).astype(np.int64) >> 3
+    hit_blocks = int(len(np.unique(g, axis=0))) if len(g) else 0
+    ray_lower_bound = hit_blocks * (512 * 5 + 16)
 
     # integration roofline: algorithmic bytes = 10 B per updated voxel (4 B sdf
     # + 1 B weight, read and written) + the depth frame + 12 B per visible
@@ -1020,6 +1147,15 @@ def run_ours(args, world, rank, local):
         except Exception as e:
             colour_rep = {"error": "%s: %s" % (type(e).__name__, e)}
 
+    # the large configuration with swapping (its own scene; reported in its
+    # own key, an error there leaves every number above intact)
+    large_rep = None
+    if extra and args.large:
+        try:
+            large_rep = run_large_section(itm, torch, dev, stream, large_frames, load_peaks()[0])
+        except Exception as e:
+            large_rep = {"error": "%s: %s" % (type(e).__name__, e)}
+
     cpu = cpu_mt = None
     if cpu_frames is not None:
         cpu = cpu_oracle_sample(cpu_frames, stride=cpu_stride, name=args.workload)
@@ -1068,6 +1204,15 @@ def run_ours(args, world, rank, local):
             "integration_voxels_updated_per_s": updated / (integ_ms / 1000.0),
             "raycast_rays_per_s": n_pix * args.steps / (float(stage[:, 2].sum()) / 1000.0),
         },
+        "raycast": {
+            "ms_mean": float(stage[:, 2].mean()),
+            "hit_blocks_last_frame": hit_blocks,
+            "unique_bytes_lower_bound": ray_lower_bound,
+            "unique_bytes_lower_bound_gbs": ray_lower_bound / (float(stage[-1, 2]) / 1000.0) / 1e9,
+            "note": "lower bound: the blocks holding a hit (512 x 5 B each) and their hash entries (16 B); the "
+                    "march reads more (blocks in front of the hits, stencil neighbours), see the ncu DRAM bytes "
+                    "of one raycast launch in profiles/raycast_kinect.md",
+        },
         "roofline": {
             "kernel": "integrate_kernel<0>",
             "bound": "hbm",
@@ -1092,6 +1237,7 @@ def run_ours(args, world, rank, local):
         "mesh": mesh_rep,
         "swapping": swap_rep,
         "colour": colour_rep,
+        "large": large_rep,
     }
     print(json.dumps(line), flush=True)
 
@@ -1109,6 +1255,8 @@ def main(argv=None):
     ap.add_argument("--no-tracking", dest="tracking", action="store_false")
     ap.add_argument("--no-mesh", dest="mesh", action="store_false")
     ap.add_argument("--no-swap", dest="swap", action="store_false")
+    ap.add_argument("--no-large", dest="large", action="store_false",
+                    help="skip the large-configuration section (corridor at 2 mm with swapping)")
     ap.add_argument("--no-colour", dest="colour", action="store_false",
                     help="skip the colour-voxel section (Sec. 3.1) on the room trajectory")
     ap.add_argument("--frames-jsonl", metavar="PATH",

@@ -32,11 +32,13 @@
 // min/max; here the fragment is the warp's tile and the atomics go to one
 // word per tile.
 //
-// The per-iteration "is the block at p allocated" query runs with the whole
-// warp converged: lanes asking for the same block are grouped with
-// __match_any_sync and one lane per group walks the hash chain (Sec. 3.3),
-// the others take its answer by shuffle.  Every arithmetic step of the march
-// uses IEEE round-to-nearest operations in a fixed order.
+// The per-iteration "is the block at p allocated" query goes through a
+// one-entry cache per lane (the last block the lane looked up); on a miss the
+// lane walks the hash chain itself (Sec. 3.3), lanes that read the same entry
+// sharing the load.  (A warp-cooperative query -- lanes grouped by block with
+// __match_any_sync, one walk per group, answers by shuffle -- measured slower:
+// few warp iterations have every lane on its cached block.)  Every arithmetic
+// step of the march uses IEEE round-to-nearest operations in a fixed order.
 #include "itm_ops.cuh"
 
 namespace itm {

@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import oracle
-from synth import kinect_workload, tiny_workload
+from synth import kinect_workload, large_workload, tiny_workload
 from tests.parity_util import compare_raycast, compare_volumes
 
 pytestmark = pytest.mark.gpu
@@ -135,6 +135,17 @@ def test_kinect_scale(itm):
     g, o, _, n_host = run(itm, w, frames, K=2048, idle=1, raycast_every=5)
     c = g.swap_counters()
     assert c["moved_out"] > 2048 and c["moved_in"] > 0
+
+
+def test_large_corridor_window(itm):
+    """The corridor at 2 mm with 2^22 buckets (the large configuration's
+    table) and a device block array of 2^18 blocks: frames 40 apart, so
+    every frame brings ~80k new blocks and the blocks left behind move out."""
+    w = large_workload()
+    p = dict(w.params, num_blocks=1 << 18)
+    g, o, _, n_host = run(itm, w, [0, 40, 80], K=1 << 16, idle=1, params=p, raycast_every=2)
+    c = g.swap_counters()
+    assert c["moved_out"] > 10000 and n_host > 10000
 
 
 def test_round_trip_equals_run_without_swapping(itm):
