@@ -420,6 +420,22 @@ int itm_mlp_pack(const float *params_dev, void *packed_dev, itm_stream stream);
 int itm_conf_weights(const float *depth_dev, const itm_intrinsics *intr, float mu, const void *packed_dev,
                      float *wpx_dev, itm_stream stream);
 
+/* One frame of the per-frame core with the learned weight (Sec. 4.2-4.4,
+ * the observation weight of the Sec. 4.3 listing replaced by w_px): the
+ * per-pixel weights (itm_conf_weights, with the scene's mu, into wpx_dev)
+ * run on the scene's second stream at the same time as the allocation on
+ * `stream` (both read only the depth frame), then itm_integrate_weighted and,
+ * with vertex_dev, itm_raycast on `stream`.  The results equal those of the
+ * four calls in sequence.  The scene must be in weight_mode 1 (whose
+ * itm_scene_create made the second stream and its events); wpx_dev is caller
+ * device memory of width x height floats, written by the call.  Asynchronous
+ * on `stream` (the second stream joins it before the integration).  Errors:
+ * ITM_ERR_ARG for null buffers, another weight mode, invalid intrinsics or
+ * pose; otherwise those of the four calls. */
+int itm_process_frame_weighted(itm_scene *scene, const float *depth_dev, const void *packed_dev, float *wpx_dev,
+                               const itm_intrinsics *intr, const float T_wc[16], float *vertex_dev,
+                               float *normal_dev, itm_stream stream);
+
 /* Features (device float[n][52]) of n pixels given by linear index
  * u + v * width (device int32[n]); out-of-range indices give zeros. */
 int itm_conf_features(const float *depth_dev, const itm_intrinsics *intr, float mu, const int32_t *pixels_dev,

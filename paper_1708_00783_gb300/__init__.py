@@ -136,6 +136,7 @@ def _load():
         "itm_track_depth": (I, [P, ip, I, ctypes.POINTER(I), fp16, P, P, ip, fp16, fp16, ctypes.POINTER(I), P, P]),
         "itm_mlp_pack": (I, [P, P, P]),
         "itm_conf_weights": (I, [P, ip, F, P, P, P]),
+        "itm_process_frame_weighted": (I, [P, P, P, P, ip, fp16, P, P, P]),
         "itm_conf_features": (I, [P, ip, F, P, I, P, P]),
         "itm_mlp_loss_grad": (I, [P, P, P, I, P, P, P, P]),
         "itm_mlp_adam": (I, [P, P, P, P, I, F, P]),
@@ -515,6 +516,14 @@ def itm_conf_weights(depth, intr, mu, packed, wpx, stream=None):
                                  _stream(stream)), "itm_conf_weights")
 
 
+def itm_process_frame_weighted(scene, depth, packed, wpx, intr, T_wc, vertex=None, normal=None, stream=None):
+    """One learned-weight frame: the per-pixel weights beside the allocation,
+    then the weighted integration and (with vertex) the raycast."""
+    a, p = _pose(T_wc)
+    _check(_lib.itm_process_frame_weighted(scene, _ptr(depth), _ptr(packed), _ptr(wpx), ctypes.byref(intr), p,
+                                           _ptr(vertex), _ptr(normal), _stream(stream)), "itm_process_frame_weighted")
+
+
 def itm_conf_features(depth, intr, mu, pixels, n, feat, stream=None):
     _check(_lib.itm_conf_features(_ptr(depth), ctypes.byref(intr), float(mu), _ptr(pixels), int(n), _ptr(feat),
                                   _stream(stream)), "itm_conf_features")
@@ -719,6 +728,16 @@ class Scene:
         _buffer(vertex, _f32_t(), 4 * _pixels(intr), "Scene.raycast: vertex")
         _buffer(normal, _f32_t(), 4 * _pixels(intr), "Scene.raycast: normal")
         itm_raycast(self.handle, intr, T_wc, vertex, normal, stream)
+
+    def process_weighted(self, depth, packed, wpx, intr, T_wc, vertex=None, normal=None, stream=None):
+        """One learned-weight frame (weight_mode 1): see itm_process_frame_weighted."""
+        import torch
+        _buffer(depth, _f32_t(), _pixels(intr), "Scene.process_weighted: depth")
+        _buffer(packed, torch.uint8, ITM_MLP_PACKED_BYTES, "Scene.process_weighted: packed")
+        _buffer(wpx, _f32_t(), _pixels(intr), "Scene.process_weighted: wpx")
+        _buffer(vertex, _f32_t(), 4 * _pixels(intr), "Scene.process_weighted: vertex")
+        _buffer(normal, _f32_t(), 4 * _pixels(intr), "Scene.process_weighted: normal")
+        itm_process_frame_weighted(self.handle, depth, packed, wpx, intr, T_wc, vertex, normal, stream)
 
     def process(self, depth, intr, T_wc, vertex=None, normal=None, stream=None):
         _buffer(depth, _f32_t(), _pixels(intr), "Scene.process: depth")

@@ -281,6 +281,11 @@ struct itm_scene {
     void *host_sdf, *host_w;
     void *swap_scratch;
     int swap_k, swap_idle;
+    // weight mode 1: a second stream and fork / join events, so that
+    // itm_process_frame_weighted runs the per-pixel weights beside the
+    // allocation (made by itm_scene_create)
+    cudaStream_t aux;
+    cudaEvent_t ev_fork, ev_join;
 };
 
 // An NVTX range named after a C-ABI call for the duration of the call, so

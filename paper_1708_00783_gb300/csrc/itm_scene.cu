@@ -162,9 +162,17 @@ int itm_scene_create(const itm_scene_params *params, itm_scene **out)
     ITM_ALLOC(d.tile_q_hdr, sizeof(int32_t) * 2 * kTileHdrInts);
     ITM_ALLOC(d.tile_q_list, sizeof(int32_t) * 2 * (size_t)kTileClasses * kOrderMaxTiles);
 #undef ITM_ALLOC
+    if (e == cudaSuccess && d.weight_mode == 1) {
+        e = cudaStreamCreateWithFlags(&sc->aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sc->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sc->ev_join, cudaEventDisableTiming);
+    }
     if (e == cudaSuccess) e = launch_reset(d, 0);
     if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
+        if (sc->ev_join) cudaEventDestroy(sc->ev_join);
+        if (sc->ev_fork) cudaEventDestroy(sc->ev_fork);
+        if (sc->aux) cudaStreamDestroy(sc->aux);
         free_dev(d);
         free(sc);
         cudaGetLastError();
@@ -181,6 +189,9 @@ int itm_scene_destroy(itm_scene *sc)
     cudaDeviceSynchronize();
     swap_free(sc);
     if (sc->d.rgbw) cudaFree(sc->d.rgbw);
+    if (sc->ev_join) cudaEventDestroy(sc->ev_join);
+    if (sc->ev_fork) cudaEventDestroy(sc->ev_fork);
+    if (sc->aux) cudaStreamDestroy(sc->aux);
     free_dev(sc->d);
     free(sc);
     return ITM_OK;
@@ -518,6 +529,32 @@ int itm_process_frame(itm_scene *sc, const float *depth_dev, const itm_intrinsic
     if (!sc || (vertex_dev && !normal_dev)) return ITM_ERR_ARG;
     int r = itm_allocate(sc, depth_dev, intr, T_wc, stream);
     if (r == ITM_OK) r = itm_integrate(sc, depth_dev, intr, T_wc, stream);
+    if (r == ITM_OK && vertex_dev) r = itm_raycast(sc, intr, T_wc, vertex_dev, normal_dev, stream);
+    return r;
+}
+
+int itm_process_frame_weighted(itm_scene *sc, const float *depth_dev, const void *packed_dev, float *wpx_dev,
+                               const itm_intrinsics *intr, const float T_wc[16], float *vertex_dev,
+                               float *normal_dev, itm_stream stream)
+{
+    Range range_("itm_process_frame_weighted");
+    if (!sc || !depth_dev || !packed_dev || !wpx_dev || (vertex_dev && !normal_dev) || !valid_intr(intr) ||
+        !valid_pose(T_wc))
+        return ITM_ERR_ARG;
+    if (sc->d.weight_mode != 1 || !sc->aux) return ITM_ERR_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    // fork: the per-pixel weights on the scene's second stream, beside the allocation
+    cudaError_t e = cudaEventRecord(sc->ev_fork, st);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sc->aux, sc->ev_fork, 0);
+    if (e != cudaSuccess) return check_cuda(e);
+    const int rc = itm_conf_weights(depth_dev, intr, sc->params.mu, packed_dev, wpx_dev, (itm_stream)sc->aux);
+    int r = itm_allocate(sc, depth_dev, intr, T_wc, stream);
+    // join, whatever failed: no work of the call stays behind on the second stream
+    e = cudaEventRecord(sc->ev_join, sc->aux);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, sc->ev_join, 0);
+    if (e != cudaSuccess) return check_cuda(e);
+    if (rc != ITM_OK) return rc;
+    if (r == ITM_OK) r = itm_integrate_weighted(sc, depth_dev, wpx_dev, intr, T_wc, stream);
     if (r == ITM_OK && vertex_dev) r = itm_raycast(sc, intr, T_wc, vertex_dev, normal_dev, stream);
     return r;
 }

@@ -202,3 +202,42 @@ def test_learned_weight_lowers_tsdf_error(itm, trained):
     print("RMS TSDF error: constant %.5f m, learned %.5f m over %d voxels" % (rc, rl, int(mc.sum())))
     assert mc.sum() > 100_000
     assert rl < rc, (rl, rc)
+
+
+def test_overlapped_frame_equals_the_calls_in_sequence(itm):
+    """itm_process_frame_weighted runs the weights beside the allocation on
+    the scene's second stream; the volume, weights and maps equal those of
+    itm_conf_weights, itm_allocate, itm_integrate_weighted and itm_raycast
+    called one after the other."""
+    import torch
+    w = kinect_workload(seed=7)
+    mu = w.params["mu"]
+    P = random_params(3)
+    packed = torch.zeros(itm.ITM_MLP_PACKED_BYTES, dtype=torch.uint8, device="cuda")
+    itm.itm_mlp_pack(dev(P), packed)
+    ci = intr_of(itm, w.intr)
+    H, W = w.intr.height, w.intr.width
+    a = itm.Scene(**dict(w.params, weight_mode=1))
+    b = itm.Scene(**dict(w.params, weight_mode=1))
+    maps = [torch.zeros((H, W, 4), dtype=torch.float32, device="cuda") for _ in range(4)]
+    wa = torch.zeros((H, W), dtype=torch.float32, device="cuda")
+    wb = torch.zeros_like(wa)
+    for k in range(4):
+        f = w.frame(k)
+        D = dev(f.depth)
+        a.process_weighted(D, packed, wa, ci, f.T_wc, maps[0], maps[1])
+        itm.itm_conf_weights(D, ci, mu, packed, wb)
+        b.allocate(D, ci, f.T_wc)
+        b.integrate(D, ci, f.T_wc, wpx=wb)
+        b.raycast(ci, f.T_wc, maps[2], maps[3])
+        torch.cuda.synchronize()
+        assert torch.equal(wa, wb)
+        assert torch.equal(maps[0], maps[2]) and torch.equal(maps[1], maps[3])
+    assert a.status() == 0 and b.status() == 0
+    ca, Fa, Wa = a.export()
+    cb, Fb, Wb = b.export()
+    ia, ib = np.lexsort(ca.T[::-1]), np.lexsort(cb.T[::-1])
+    assert np.array_equal(ca[ia], cb[ib]) and np.array_equal(Fa[ia], Fb[ib]) and np.array_equal(Wa[ia], Wb[ib])
+    plain = itm.Scene(**w.params)
+    with pytest.raises(itm.ItmError):
+        plain.process_weighted(D, packed, wa, ci, f.T_wc)
