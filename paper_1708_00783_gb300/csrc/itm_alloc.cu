@@ -41,11 +41,13 @@ __global__ void __launch_bounds__(256) alloc_enumerate_kernel(SceneDev s, const 
                                                               float *__restrict__ depth_out)
 {
     const int cta = blockIdx.y * gridDim.x + blockIdx.x, ctas = gridDim.x * gridDim.y;
+    grid_dep_wait();  // the previous raycast may still read the range tiles
     for (int i = cta * blockDim.x + threadIdx.x; i < n_range_tiles; i += ctas * blockDim.x) {
         s.range_min[i] = 0xffffffffu;
         s.range_max[i] = 0u;
     }
     enumerate_tile(s, depth, in, T, inv_b, blockIdx.x, blockIdx.y, raw, depth_out);
+    grid_dep_launch();
 }
 
 // The last CTA to finish its requests then resolves the overflow list (its
@@ -53,6 +55,7 @@ __global__ void __launch_bounds__(256) alloc_enumerate_kernel(SceneDev s, const 
 __global__ void __launch_bounds__(256) alloc_commit_kernel(SceneDev s)
 {
     __shared__ int is_last, remaining;
+    grid_dep_wait();
     const int n = min(__ldcg(&s.ctr->n_req), s.nb);
     const int stride = gridDim.x * blockDim.x;
     for (int i0 = blockIdx.x * blockDim.x; i0 < n; i0 += stride) {
@@ -67,10 +70,12 @@ __global__ void __launch_bounds__(256) alloc_commit_kernel(SceneDev s)
         __threadfence();
         overflow_scene(s, remaining);
     }
+    grid_dep_launch();
 }
 
 __global__ void __launch_bounds__(256) build_visible_kernel(SceneDev s, Mat34 M, Intr in)
 {
+    grid_dep_wait();
     const int n = min(__ldcg(&s.ctr->block_head), s.nv);
     const float zfar = visible_zfar(s);
     const int groups = gridDim.x * (blockDim.x >> 3);
@@ -78,6 +83,7 @@ __global__ void __launch_bounds__(256) build_visible_kernel(SceneDev s, Mat34 M,
         const int i = g0 + (threadIdx.x >> 3);
         visible_8<false>(s, M, in, zfar, i < n, i, 0.0f, 1, 1);
     }
+    grid_dep_launch();
 }
 
 // The same, also filling the search range of a raycast from this pose (the
@@ -85,6 +91,7 @@ __global__ void __launch_bounds__(256) build_visible_kernel(SceneDev s, Mat34 M,
 __global__ void __launch_bounds__(256) build_visible_range_kernel(SceneDev s, Mat34 M, Intr in, float zc,
                                                                   int tiles_x, int tiles_y)
 {
+    grid_dep_wait();
     const int n = min(__ldcg(&s.ctr->block_head), s.nv);
     const float zfar = visible_zfar(s);
     const int groups = gridDim.x * (blockDim.x >> 3);
@@ -92,6 +99,7 @@ __global__ void __launch_bounds__(256) build_visible_range_kernel(SceneDev s, Ma
         const int i = g0 + (threadIdx.x >> 3);
         visible_8<true>(s, M, in, zfar, i < n, i, zc, tiles_x, tiles_y);
     }
+    grid_dep_launch();
 }
 
 int sm_count()
@@ -119,29 +127,34 @@ int persistent_grid(int threads, const void *kernel)
 cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &in, const Mat34 &T_wc,
                             const Mat34 &M_d, bool with_range, cudaStream_t st, const uint16_t *raw)
 {
-    cudaError_t e = cudaMemsetAsync(reinterpret_cast<char *>(s.ctr) + kFrameCountersOffset, 0,
-                                    kFrameCountersBytes, st);
+    static_assert(kFrameCountersOffset % 4 == 0 && kFrameCountersBytes % 4 == 0, "word-aligned frame counters");
+    cudaError_t e = launch_pdl(zero_words_kernel, dim3(1), dim3(32), 0, st,
+                               reinterpret_cast<int32_t *>(reinterpret_cast<char *>(s.ctr) + kFrameCountersOffset),
+                               (int)(kFrameCountersBytes / 4));
     if (e != cudaSuccess) return e;
     const float inv_b = (float)(1.0 / (8.0 * (double)s.voxel_size));
     dim3 grid((in.W + 31) / 32, (in.H + 7) / 8);
     const int n_range_tiles = with_range ? ((in.W + 7) / 8) * ((in.H + 3) / 4) : 0;
     // with raw, depth is the output of the frame's conversion
-    alloc_enumerate_kernel<<<grid, 256, 0, st>>>(s, raw ? nullptr : depth, in, T_wc, inv_b, n_range_tiles, raw,
-                                                 raw ? const_cast<float *>(depth) : nullptr);
+    e = launch_pdl(alloc_enumerate_kernel, grid, dim3(256), 0, st, s, raw ? nullptr : depth, in, T_wc, inv_b,
+                   n_range_tiles, raw, raw ? const_cast<float *>(depth) : nullptr);
+    if (e != cudaSuccess) return e;
     static int g_commit = 0, g_visible = 0, g_visrange = 0;
     // one CTA per SM: a frame's requests (usually a few thousand) fit in one
     // pass, and fewer CTAs pay the completion count's fences
     if (!g_commit) g_commit = sm_count();
     if (!g_visible) g_visible = persistent_grid(256, (const void *)build_visible_kernel);
     if (!g_visrange) g_visrange = persistent_grid(256, (const void *)build_visible_range_kernel);
-    alloc_commit_kernel<<<g_commit, 256, 0, st>>>(s);
+    e = launch_pdl(alloc_commit_kernel, dim3(g_commit), dim3(256), 0, st, s);
+    if (e != cudaSuccess) return e;
     if (with_range) {
         const int tx = (in.W + 7) / 8, ty = (in.H + 3) / 4;
-        build_visible_range_kernel<<<g_visrange, 256, 0, st>>>(s, M_d, in, s.z_min - 1e-3f, tx, ty);
+        e = launch_pdl(build_visible_range_kernel, dim3(g_visrange), dim3(256), 0, st, s, M_d, in, s.z_min - 1e-3f,
+                       tx, ty);
     } else {
-        build_visible_kernel<<<g_visible, 256, 0, st>>>(s, M_d, in);
+        e = launch_pdl(build_visible_kernel, dim3(g_visible), dim3(256), 0, st, s, M_d, in);
     }
-    return cudaGetLastError();
+    return e;
 }
 
 int overflow_capacity() { return kOvfCapacity; }

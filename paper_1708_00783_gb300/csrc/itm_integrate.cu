@@ -46,6 +46,7 @@ __global__ void __launch_bounds__(kThreads) integrate_kernel(SceneDev s, const f
         fill_rcp_w(rcp_w);
         __syncthreads();
     }
+    grid_dep_wait();
     const int n = min(__ldcg(&s.ctr->n_visible), s.nv);
     const int t = threadIdx.x;
     unsigned updated = 0;
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(kThreads) integrate_kernel(SceneDev s, const f
         row = row_next;
     }
 
+    grid_dep_launch();
     // counters: one atomic per warp
     for (int o = 16; o > 0; o >>= 1) updated += __shfl_xor_sync(kFull, updated, o);
     if ((t & 31) == 0 && updated) atomicAdd(&s.ctr->updated, (unsigned long long)updated);
@@ -106,9 +108,11 @@ cudaError_t launch_integrate(const SceneDev &s, const float *depth, const float 
                              const Mat34 &M_d, cudaStream_t st)
 {
     const float2 nz = make_float2(-0.0f, -0.0f);
-    if (wpx) integrate_kernel<1><<<integrate_grid<1>(), kThreads, 0, st>>>(s, depth, wpx, in, M_d, nz);
-    else integrate_kernel<0><<<integrate_grid<0>(), kThreads, 0, st>>>(s, depth, nullptr, in, M_d, nz);
-    return cudaGetLastError();
+    if (wpx)
+        return launch_pdl(integrate_kernel<1>, dim3(integrate_grid<1>()), dim3(kThreads), 0, st, s, depth, wpx, in,
+                          M_d, nz);
+    return launch_pdl(integrate_kernel<0>, dim3(integrate_grid<0>()), dim3(kThreads), 0, st, s, depth,
+                      (const float *)nullptr, in, M_d, nz);
 }
 
 }  // namespace itm

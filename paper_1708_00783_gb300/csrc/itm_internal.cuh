@@ -226,6 +226,44 @@ __device__ __forceinline__ bool shard_owns(const SceneDev &s, int bx)
     return s.shard_n <= 1 || slab_owner(bx, s.shard_n, s.shard_w) == s.shard_i;
 }
 
+// ------------------------------------------ programmatic dependent launch
+// The per-frame kernels are launched with programmatic stream serialization
+// (launch_pdl): a kernel may be scheduled while the kernel before it on the
+// stream drains, runs only what touches no memory until grid_dep_wait()
+// (which returns once the previous kernel has completed and its writes are
+// visible), and calls grid_dep_launch() when its own main work is done so
+// that the next kernel can be scheduled early.  Both are no-ops for a kernel
+// launched the ordinary way.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st, Args... args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+namespace {
+// Zeroes n 32-bit words at p after the previous kernel (a launch_pdl stand-in
+// for cudaMemsetAsync, which would break the chain of dependent launches).
+__global__ void __launch_bounds__(32) zero_words_kernel(int32_t *p, int n)
+{
+    grid_dep_wait();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = 0;
+    grid_dep_launch();
+}
+}  // namespace
+
 // ------------------------------------------------ IEEE round-to-nearest ops
 // Every operation that decides an integer (which block, which pixel, whether
 // a voxel is updated) is written with these so that no multiply-add is fused.

@@ -87,6 +87,7 @@ __global__ void __launch_bounds__(256, 4) raycast_dynamic_kernel(SceneDev s, Int
     // first position of each class slot k (class kTileClasses - 1 - k)
     __shared__ int first[kTileClasses + 1];
     const int lane = threadIdx.x & 31;
+    grid_dep_wait();
     if (use_order) {
         if (threadIdx.x == 0) {
             int acc = 0;
@@ -105,7 +106,10 @@ __global__ void __launch_bounds__(256, 4) raycast_dynamic_kernel(SceneDev s, Int
         int t = 0;
         if (lane == 0) t = atomicAdd(&hdr_w[0], 1);
         t = __shfl_sync(kFull, t, 0);
-        if (t >= n_tiles) return;
+        if (t >= n_tiles) {
+            grid_dep_launch();
+            return;
+        }
         int tile = t;
         if (use_order) {
             int k = 0;
@@ -180,7 +184,7 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
         int32_t *hdr_w = s.tile_q_hdr + w * kTileHdrInts, *list_w = s.tile_q_list + (size_t)w * kTileClasses * kOrderMaxTiles;
         const int32_t *hdr_r = s.tile_q_hdr + (1 - w) * kTileHdrInts;
         const int32_t *list_r = s.tile_q_list + (size_t)(1 - w) * kTileClasses * kOrderMaxTiles;
-        if (e == cudaSuccess) e = cudaMemsetAsync(hdr_w, 0, sizeof(int32_t) * kTileHdrInts, st);
+        if (e == cudaSuccess) e = launch_pdl(zero_words_kernel, dim3(1), dim3(32), 0, st, hdr_w, kTileHdrInts);
         if (e != cudaSuccess) return e;
         static int g_dyn[2] = {0, 0};
         const int mode = s.weight_mode ? 1 : 0;
@@ -196,15 +200,15 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
         const int g = g_dyn[mode] < (n_tiles + 7) / 8 ? g_dyn[mode] : (n_tiles + 7) / 8;
         const bool write_order = n_tiles <= kOrderMaxTiles;
         const bool use_order = write_order && order_dims[0] == tx && order_dims[1] == ty;
+        const float tBm = tB_m;
         if (mode == 0)
-            raycast_dynamic_kernel<0><<<g, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
-                                                         s.range_max, tx, n_tiles, hdr_w, list_w, hdr_r, list_r,
-                                                         use_order, write_order);
+            e = launch_pdl(raycast_dynamic_kernel<0>, dim3(g), dim3(256), 0, st, s, in, T_wc, vtx, nrm, max_iter, tBm,
+                           inv_sv, (const uint32_t *)s.range_min, (const uint32_t *)s.range_max, tx, n_tiles, hdr_w,
+                           list_w, hdr_r, list_r, use_order, write_order);
         else
-            raycast_dynamic_kernel<1><<<g, 256, 0, st>>>(s, in, T_wc, vtx, nrm, max_iter, tB_m, inv_sv, s.range_min,
-                                                         s.range_max, tx, n_tiles, hdr_w, list_w, hdr_r, list_r,
-                                                         use_order, write_order);
-        e = cudaGetLastError();
+            e = launch_pdl(raycast_dynamic_kernel<1>, dim3(g), dim3(256), 0, st, s, in, T_wc, vtx, nrm, max_iter, tBm,
+                           inv_sv, (const uint32_t *)s.range_min, (const uint32_t *)s.range_max, tx, n_tiles, hdr_w,
+                           list_w, hdr_r, list_r, use_order, write_order);
         if (e != cudaSuccess) return e;
         if (write_order) {
             order_dims[0] = tx;
