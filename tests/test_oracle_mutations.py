@@ -24,6 +24,7 @@ COLOUR = "test_oracle_colour_pins.py"
 COMB = "test_oracle_combined_pins.py"
 TRACK = "test_oracle_track_pins.py"
 MESH = "test_oracle_mesh_pins.py"
+SHARD = "test_oracle_shard_pins.py"
 
 # (pin module, mistake, original text, planted text)
 MUTANTS = [
@@ -242,6 +243,16 @@ MUTANTS = [
      "                    int axis = (c - a) == 2 ? 0 : (c - a) == 1 ? 1 : 2;"),
     (MESH, "corner offset on the wrong axis", "                        float coord = (float)(g[k] + ((a >> k) & 1));",
      "                        float coord = (float)(g[k] + ((a >> ((k + 1) % 3)) & 1));"),
+    # a scene split over processes by slabs of block columns
+    (SHARD, "slab owner by truncation", "    int q = bx >= 0 ? bx / w : -((-bx + w - 1) / w); /* floor(bx / w) */",
+     "    int q = bx / w;"),
+    (SHARD, "no ghost columns", "#define ORC_SHARD_GHOST 1", "#define ORC_SHARD_GHOST 0"),
+    (SHARD, "hits in other parts' columns reported",
+     "            if (!shard_owns(s, ((int)floorf(q[0] + 0.5f)) >> 3)) continue; /* another part's hit */\n", ""),
+    (SHARD, "merge keeps the farthest hit", "            if (best < 0 || z < best_z) {", "            if (best < 0 || z > best_z) {"),
+    (SHARD, "merge ties to the higher part", "            if (best < 0 || z < best_z) {", "            if (best < 0 || z <= best_z) {"),
+    (SHARD, "merge depth from the wrong row", "            const float z = row_apply(&M[8], V[0], V[1], V[2]);",
+     "            const float z = row_apply(&M[4], V[0], V[1], V[2]);"),
 ]
 
 
