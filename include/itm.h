@@ -73,7 +73,7 @@ typedef struct {
 /* Scene parameters (Sec. 6 ITMSceneParams; Sec. 3.1 voxel block array size;
  * Sec. 3.2 bucket count; Sec. 4.3 mu and maxW).
  *  voxel_size  metres per voxel (s); a block is 8 voxels per axis
- *  mu          truncation band (metres)
+ *  mu          truncation band (metres), 2^-64 <= mu < 2^64
  *  max_w       weight cap; 1..255 in weight_mode 0
  *  num_buckets ordered part of the hash table, a power of two
  *  num_excess  unordered excess entries

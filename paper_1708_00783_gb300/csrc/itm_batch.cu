@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(256) batch_integrate_kernel(const ItemDev *__r
     for (int vb = blockIdx.x * per + (threadIdx.x >> 6); vb < total; vb += gridDim.x * per) {
         const int k = find_item(prefix, n, vb);
         const ItemDev &it = items[k];
-        const int ptr = __ldg(&it.s.visible[vb - prefix[k]]);
+        const int ptr = vis_ptr(__ldg(&it.s.visible[vb - prefix[k]]));
         const short4 b = __ldg(&it.s.block_pos[ptr]);
         unsigned updated = 0;
         const RowData row = load_row<0>(it.s, ptr, t);
@@ -519,6 +519,7 @@ int itm_batch_run(itm_batch *b, const itm_batch_item *items, int n, itm_stream s
     for (int i = 0; i < n; ++i) {
         items[i].scene->last_stream = st;
         items[i].scene->alloc_epoch++;  // the batch rewrote the scene's range tiles
+        items[i].scene->vis_ok = false;  // and its visible list
     }
     return check_cuda(e);
 }

@@ -85,8 +85,8 @@ __global__ void __launch_bounds__(kThreads) colour_kernel(SceneDev s, const floa
     const float umax = (float)(in.W - 2), vmax = (float)(in.H - 2);
     const float max_w = (float)s.max_w;
     for (int i = blockIdx.x; i < n; i += gridDim.x) {
-        const int ptr = __ldg(&s.visible[i]);
-        if (ptr < 0 || ptr >= s.nv) continue;
+        const int ptr = vis_ptr(__ldg(&s.visible[i]));
+        if (ptr >= s.nv) continue;
         const short4 b = __ldg(&s.block_pos[ptr]);
         const float py = fmul((float)(b.y * 8 + ly), vs);
         const float pz = fmul((float)(b.z * 8 + lz), vs);
@@ -199,7 +199,7 @@ int itm_integrate_colour(itm_scene *sc, const float *depth_dev, const itm_intrin
     cudaStream_t st = (cudaStream_t)stream;
     sc->last_stream = st;
     const Intr in = to_intr(intr);
-    cudaError_t e = launch_integrate(sc->d, depth_dev, nullptr, in, M, st);
+    cudaError_t e = launch_integrate(sc->d, depth_dev, nullptr, in, M, interior_flags_hold(sc, T_wc, intr), st);
     if (e != cudaSuccess) return check_cuda(e);
     ColourFrame cf;
     cf.rgb = rgb_dev;

@@ -24,6 +24,10 @@
 // pixel index is truncated by a round-toward-zero add of 2^23 instead of
 // conversion instructions.
 //
+// Blocks that the visible list marks interior (kVisInterior), when the list
+// was built for this pose and intrinsics (interior_ok, decided by the host),
+// skip the per-voxel image-bounds and reciprocal-range tests.
+//
 // The decision needs no voxel data: a thread loads a 16-byte quad of sdf
 // only when one of its four voxels is updated (and its 8 bytes of weights
 // when any of its eight is), and stores it back after the update.  Skipped
@@ -39,7 +43,7 @@ constexpr int kThreads = 64;
 template <int MODE>  // 0: constant weight 1, uint8 weights; 1: per-pixel weight, float weights
 __global__ void __launch_bounds__(kThreads) integrate_kernel(SceneDev s, const float *__restrict__ depth,
                                                              const float *__restrict__ wpx, Intr in, Mat34 M,
-                                                             float2 nz)
+                                                             float2 nz, int interior_ok)
 {
     __shared__ float2 rcp_w[256];
     if (MODE == 0) {
@@ -51,29 +55,32 @@ __global__ void __launch_bounds__(kThreads) integrate_kernel(SceneDev s, const f
     const int t = threadIdx.x;
     unsigned updated = 0;
     int i = blockIdx.x;
-    int ptr = 0;
+    int e = 0;  // visible-list entry: block index and interior flag
     short4 b = make_short4(0, 0, 0, 0);
     RowData row;
     if (i < n) {
-        ptr = __ldg(&s.visible[i]);
-        b = __ldg(&s.block_pos[ptr]);
-        row = load_row<MODE>(s, ptr, t);
+        e = __ldg(&s.visible[i]);
+        b = __ldg(&s.block_pos[vis_ptr(e)]);
+        row = load_row<MODE>(s, vis_ptr(e), t);
     }
     while (i < n) {
         // the next block's index, coordinates and row data are requested
         // before this block's update, which hides their latency
         const int i_next = i + gridDim.x;
-        int ptr_next = 0;
+        int e_next = 0;
         short4 b_next = b;
         RowData row_next = row;
         if (i_next < n) {
-            ptr_next = __ldg(&s.visible[i_next]);
-            b_next = __ldg(&s.block_pos[ptr_next]);
-            row_next = load_row<MODE>(s, ptr_next, t);
+            e_next = __ldg(&s.visible[i_next]);
+            b_next = __ldg(&s.block_pos[vis_ptr(e_next)]);
+            row_next = load_row<MODE>(s, vis_ptr(e_next), t);
         }
-        integrate_block<MODE>(s, depth, wpx, in, M, ptr, b, t, updated, row, rcp_w, nz);
+        if (interior_ok && (e & kVisInterior))
+            integrate_block<MODE, true>(s, depth, wpx, in, M, vis_ptr(e), b, t, updated, row, rcp_w, nz);
+        else
+            integrate_block<MODE, false>(s, depth, wpx, in, M, vis_ptr(e), b, t, updated, row, rcp_w, nz);
         i = i_next;
-        ptr = ptr_next;
+        e = e_next;
         b = b_next;
         row = row_next;
     }
@@ -105,14 +112,15 @@ int integrate_grid()
 }  // namespace
 
 cudaError_t launch_integrate(const SceneDev &s, const float *depth, const float *wpx, const Intr &in,
-                             const Mat34 &M_d, cudaStream_t st)
+                             const Mat34 &M_d, bool interior_ok, cudaStream_t st)
 {
     const float2 nz = make_float2(-0.0f, -0.0f);
+    const int io = interior_ok ? 1 : 0;
     if (wpx)
         return launch_pdl(integrate_kernel<1>, dim3(integrate_grid<1>()), dim3(kThreads), 0, st, s, depth, wpx, in,
-                          M_d, nz);
+                          M_d, nz, io);
     return launch_pdl(integrate_kernel<0>, dim3(integrate_grid<0>()), dim3(kThreads), 0, st, s, depth,
-                      (const float *)nullptr, in, M_d, nz);
+                      (const float *)nullptr, in, M_d, nz, io);
 }
 
 }  // namespace itm

@@ -314,6 +314,12 @@ struct itm_scene {
     // tiles_y image ({0, 0}: none yet); the next raycast writes side order_side
     int order_dims[2];
     int order_side;
+    // the visible list's interior flags were computed for vis_pose /
+    // vis_intr (vis_ok: by the last allocation, with no block moved or freed
+    // since)
+    bool vis_ok;
+    float vis_pose[16];
+    itm_intrinsics vis_intr;
     // Sec. 5 swapping (itm_swap_enable): the host store (pinned, mapped) and
     // the device scratch of the selection
     void *host_sdf, *host_w;
@@ -340,14 +346,19 @@ void pose_rows(const float T[16], Mat34 &out);        // rows 0..2 of T
 void rigid_inverse_rows(const float T[16], Mat34 &out); // rows 0..2 of T^-1 (fp64, rounded once)
 int valid_intr(const itm_intrinsics *in);
 Intr to_intr(const itm_intrinsics *in);
+// the visible list's interior flags hold for an integration with this pose
+// and these intrinsics (launch_integrate's interior_ok)
+bool interior_flags_hold(const itm_scene *sc, const float T_wc[16], const itm_intrinsics *intr);
 }  // namespace itm
 
 // Launchers implemented in the kernel translation units.
 namespace itm {
 cudaError_t launch_allocate(const SceneDev &s, const float *depth, const Intr &in, const Mat34 &T_wc,
                             const Mat34 &M_d, bool with_range, cudaStream_t st, const uint16_t *raw = nullptr);
+// interior_ok: the visible list was built by an allocation with this pose and
+// these intrinsics, and no block changed since, so its interior flags hold
 cudaError_t launch_integrate(const SceneDev &s, const float *depth, const float *wpx, const Intr &in,
-                             const Mat34 &M_d, cudaStream_t st);
+                             const Mat34 &M_d, bool interior_ok, cudaStream_t st);
 cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc, const Mat34 &M_d, float4 *vtx,
                            float4 *nrm, bool range_ready, int order_dims[2], int &order_side, cudaStream_t st);
 cudaError_t launch_raycast_range(const SceneDev &s, const Intr &in, const Mat34 &M_d, uint32_t *rmin, uint32_t *rmax,

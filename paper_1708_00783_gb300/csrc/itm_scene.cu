@@ -55,6 +55,12 @@ static int valid_pose(const float *T)
     return 1;
 }
 
+bool interior_flags_hold(const itm_scene *sc, const float T_wc[16], const itm_intrinsics *intr)
+{
+    return sc->vis_ok && memcmp(sc->vis_pose, T_wc, sizeof(sc->vis_pose)) == 0 &&
+           memcmp(&sc->vis_intr, intr, sizeof(itm_intrinsics)) == 0;
+}
+
 Intr to_intr(const itm_intrinsics *in)
 {
     Intr r;
@@ -71,6 +77,8 @@ static int valid_params(const itm_scene_params *p)
 {
     if (!p) return 0;
     if (!(p->voxel_size > 0.0f) || !(p->mu > 0.0f)) return 0;
+    // eta / mu is taken from RN(1 / mu) with residual corrections, exact for mu in this range
+    if (!(p->mu >= 0x1p-64f && p->mu < 0x1p64f)) return 0;
     if (p->weight_mode != 0 && p->weight_mode != 1) return 0;
     if (p->max_w < 1 || (p->weight_mode == 0 && p->max_w > 255)) return 0;
     if (p->num_buckets < 1 || p->num_buckets > (1 << 30) || (p->num_buckets & (p->num_buckets - 1))) return 0;
@@ -202,6 +210,7 @@ int itm_scene_reset(itm_scene *sc, itm_stream stream)
     Range range_("itm_scene_reset");
     if (!sc) return ITM_ERR_ARG;
     sc->alloc_epoch++;
+    sc->vis_ok = false;
     cudaStream_t st = (cudaStream_t)stream;
     sc->last_stream = st;
     cudaError_t e = launch_reset(sc->d, st);
@@ -223,8 +232,15 @@ static int allocate_impl(itm_scene *sc, const float *depth_dev, const uint16_t *
     const Intr in = to_intr(intr);
     const bool with_range = range_fits(in);
     sc->alloc_epoch++;
+    sc->vis_ok = false;
     if (sc->d.swap_state) sc->d.swap_frame++;  // Sec. 5: the blocks this allocation meets are stamped with it
     const int r = check_cuda(launch_allocate(sc->d, depth_dev, in, T, M, with_range, st, raw_dev));
+    if (r == ITM_OK) {
+        // the visible list's interior flags hold for this pose and these intrinsics
+        sc->vis_ok = true;
+        memcpy(sc->vis_pose, T_wc, sizeof(sc->vis_pose));
+        sc->vis_intr = *intr;
+    }
     if (r == ITM_OK && with_range) {
         // the range tiles now hold the range of a raycast from this pose
         sc->range_epoch = sc->alloc_epoch;
@@ -259,7 +275,7 @@ int itm_integrate(itm_scene *sc, const float *depth_dev, const itm_intrinsics *i
     rigid_inverse_rows(T_wc, M);
     cudaStream_t st = (cudaStream_t)stream;
     sc->last_stream = st;
-    return check_cuda(launch_integrate(sc->d, depth_dev, nullptr, to_intr(intr), M, st));
+    return check_cuda(launch_integrate(sc->d, depth_dev, nullptr, to_intr(intr), M, interior_flags_hold(sc, T_wc, intr), st));
 }
 
 int itm_integrate_weighted(itm_scene *sc, const float *depth_dev, const float *wpx_dev, const itm_intrinsics *intr,
@@ -272,7 +288,7 @@ int itm_integrate_weighted(itm_scene *sc, const float *depth_dev, const float *w
     rigid_inverse_rows(T_wc, M);
     cudaStream_t st = (cudaStream_t)stream;
     sc->last_stream = st;
-    return check_cuda(launch_integrate(sc->d, depth_dev, wpx_dev, to_intr(intr), M, st));
+    return check_cuda(launch_integrate(sc->d, depth_dev, wpx_dev, to_intr(intr), M, interior_flags_hold(sc, T_wc, intr), st));
 }
 
 int itm_raycast(itm_scene *sc, const itm_intrinsics *intr, const float T_wc[16], float *vertex_dev,
@@ -735,6 +751,7 @@ int itm_scene_import(itm_scene *sc, const int16_t *coords_host, const float *sdf
         }
     }
     sc->alloc_epoch++;
+    sc->vis_ok = false;
     cudaError_t e = cudaStreamSynchronize(sc->last_stream);
     if (e == cudaSuccess) e = launch_reset(d, 0);
     if (e == cudaSuccess) e = swap_reset(sc, 0);

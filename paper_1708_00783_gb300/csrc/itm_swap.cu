@@ -545,6 +545,7 @@ int itm_swap_out(itm_scene *sc, itm_stream stream)
 {
     Range range_("itm_swap_out");
     if (!sc || !sc->d.swap_state) return ITM_ERR_ARG;
+    sc->vis_ok = false;  // blocks are freed: the visible list's interior flags lapse
     cudaStream_t st = (cudaStream_t)stream;
     sc->last_stream = st;
     const SwapDev w = swap_dev(sc);

@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from synth import Intrinsics, kinect_workload, large_workload, tiny_workload
-from tests.parity_util import compare_raycast, compare_volumes
+from tests.parity_util import compare_raycast, compare_volumes, key_of
 from tests.test_oracle_pins import check_hash_invariants
 
 pytestmark = pytest.mark.gpu
@@ -383,3 +383,50 @@ def test_raycast_independent_of_tile_order(itm):
     vo, no = o.raycast(W, H, w.intr.as_array(), T)
     rep = compare_raycast(outs[0][0], outs[0][1], vo, no, T)
     assert rep["hits"] > 0
+
+
+def _rot_y(deg):
+    a = np.radians(deg)
+    R = np.eye(4)
+    R[0, 0] = R[2, 2] = np.cos(a)
+    R[0, 2], R[2, 0] = np.sin(a), -np.sin(a)
+    return R
+
+
+@pytest.mark.parametrize("change", ["pose", "intrinsics"])
+def test_integration_at_another_pose_than_the_allocation(itm, change):
+    """The visible list marks blocks whose voxels all project inside the image
+    for the allocation's pose and intrinsics, and the integration then skips
+    their bounds tests.  Integrating at another pose (10 degrees of yaw) or
+    with other intrinsics (cx shifted by 40 px) must not use those marks:
+    every block the GPU changes equals the oracle's integration of it at the
+    new pose (the oracle integrates every allocated block, the GPU the
+    allocation's visible list, so only the blocks the GPU changed compare)."""
+    w = kinect_workload(seed=3)
+    g, o, _ = run_pair(itm, w, range(3))
+    ci = intr_of(itm, w.intr)
+    ia = w.intr.as_array()
+    f = w.frame(3)
+    d = dev(f.depth)
+    g.allocate(d, ci, f.T_wc)
+    o.allocate(f.depth, ia, f.T_wc)
+    T2, ci2, ia2 = f.T_wc, ci, ia
+    if change == "pose":
+        T2 = (np.asarray(f.T_wc, np.float64) @ _rot_y(10.0)).astype(np.float32)
+    else:
+        i2 = w.intr
+        ci2 = itm.make_intrinsics(i2.width, i2.height, i2.fx, i2.fy, i2.cx + 40.0, i2.cy)
+        ia2 = np.array([i2.fx, i2.fy, i2.cx + 40.0, i2.cy], dtype=np.float32)
+    before = g.export()
+    g.integrate(d, ci2, T2)
+    o.integrate(f.depth, ia2, T2)
+    after = g.export()
+    cg, Fg, Wg = after
+    assert np.array_equal(before[0], cg)
+    changed = np.any(Wg != before[2], axis=1)
+    assert changed.sum() > 1000
+    co, Fo, Wo = o.export()
+    pos = {k: i for i, k in enumerate(key_of(co).tolist())}
+    io = np.array([pos[k] for k in key_of(cg[changed]).tolist()])
+    assert np.array_equal(Wg[changed], Wo[io])
+    assert np.abs(Fg[changed] - Fo[io]).max() <= 1e-4
