@@ -887,7 +887,7 @@ def run_learned_section(itm, torch, dev, conf_frames):
     stream = torch.cuda.current_stream()
     sc_l = itm.Scene(**dict(w.params, weight_mode=1))
     sc_c = itm.Scene(**w.params)
-    stage = []
+    stage, plain = [], []
     for k in keys:
         T = ev[k][1]
         e = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
@@ -902,11 +902,17 @@ def run_learned_section(itm, torch, dev, conf_frames):
         e[4].record(stream)
         stage.append(e)
         flush.zero_()
-        itm.itm_process_frame(sc_c.handle, dd[k], ci, T, None, None, stream)
+        # the constant weight on the same frames: itm_process_frame on a plain scene
+        ec = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ec[0].record(stream)
+        itm.itm_process_frame(sc_c.handle, dd[k], ci, T, vtx, nrm, stream)
+        ec[1].record(stream)
+        plain.append(ec)
         flush.zero_()
     torch.cuda.synchronize()
     st = np.array([[e[j].elapsed_time(e[j + 1]) for j in range(4)] for e in stage])
     ms = float(st.sum(axis=1).mean())
+    ms_plain = float(np.mean([a.elapsed_time(b) for a, b in plain]))
     # the same frames through itm_process_frame_weighted on a third scene: the
     # weights run on the scene's second stream beside the allocation
     sc_o = itm.Scene(**dict(w.params, weight_mode=1))
@@ -929,6 +935,8 @@ def run_learned_section(itm, torch, dev, conf_frames):
         "workload": "room seed 7, 640x480 @ 5 mm, 30 frames (0, 2, ..., 58) with noise and flying pixels",
         "frames_per_s": 1000.0 / ms_over,
         "frames_per_s_calls_in_sequence": 1000.0 / ms,
+        "plain_frames_per_s_same_frames": 1000.0 / ms_plain,
+        "learned_time_over_plain": ms_over / ms_plain,
         "overlap": "itm_process_frame_weighted: the per-pixel weights on the scene's second stream beside the "
                    "allocation, joined before the weighted integration (last frame's weight map equal to the "
                    "sequential run's: %s)" % same,
