@@ -1292,8 +1292,8 @@ def run_ours(args, world, rank, local):
         "clocks": clocks,
         "e2e": e2e,
         # per frame: counter reset, enumerate (+ u16), commit (+ overflow), visible + range, integrate, tile
-        # queue reset, raycast
-        "gpu_launches": 7 * args.steps,
+        # queue reset, raycast march, raycast finish
+        "gpu_launches": 8 * args.steps,
         "batched": batched_rep,
         "learned": learned_rep,
         "tracking": tracking_rep,

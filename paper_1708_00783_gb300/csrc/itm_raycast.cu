@@ -66,9 +66,12 @@ __global__ void __launch_bounds__(256) range_kernel(SceneDev s, Mat34 M, Intr in
     }
 }
 
-// Persistent raycast: each warp takes the next 8x4 tile from a device counter
-// until none is left, so warps that finish early pick up more work instead of
-// idling behind the slowest tiles of a fixed grid.  With use_order the tiles
+// Persistent raycast, first phase (the march): each warp takes the next 8x4
+// tile from a device counter until none is left, so warps that finish early
+// pick up more work instead of idling behind the slowest tiles of a fixed
+// grid.  raycast_finish_kernel then refines the hits and takes their normals
+// (two kernels with smaller code each measured faster than the one that did
+// both).  With use_order the tiles
 // are handed out from the queues of the previous raycast, heaviest cost class
 // first (longest processing time first), so the expensive tiles do not start
 // last.  With write_order each finished tile is appended to the queue of its
@@ -117,14 +120,28 @@ __global__ void __launch_bounds__(256, 4) raycast_dynamic_kernel(SceneDev s, Int
             tile = __ldg(&list_r[(size_t)(kTileClasses - 1 - k) * kOrderMaxTiles + (t - first[k])]);
             if ((unsigned)tile >= (unsigned)n_tiles) tile = t;
         }
-        const int cost = raycast_warp_tile<MODE, true>(s, in, T, vtx, nrm, max_iter, tB_m, inv_sv, rmin, rmax,
-                                                       tiles_x, tile % tiles_x, tile / tiles_x);
+        const int cost = raycast_warp_tile<MODE, true, 1>(s, in, T, vtx, nrm, max_iter, tB_m, inv_sv, rmin, rmax,
+                                                          tiles_x, tile % tiles_x, tile / tiles_x);
         if (write_order && lane == 0) {
             const int c = min(cost >> 3, kTileClasses - 1);
             const int p = atomicAdd(&hdr_w[1 + c], 1);
             list_w[(size_t)c * kOrderMaxTiles + p] = tile;
         }
     }
+}
+
+// second phase of the split raycast: refinement, hit point and normal of the
+// pixels whose march (raycast_dynamic_kernel) ended behind the surface
+template <int MODE>
+__global__ void __launch_bounds__(256, 4) raycast_finish_kernel(SceneDev s, Intr in, Mat34 T, float4 *__restrict__ vtx,
+                                                             float4 *__restrict__ nrm, int max_iter, float tB_m,
+                                                             float inv_sv)
+{
+    grid_dep_wait();
+    const int warp = threadIdx.x >> 5;
+    const int tix = blockIdx.x * 4 + (warp & 3), tiy = blockIdx.y * 2 + (warp >> 2);
+    if (tix >= (in.W + 7) / 8 || tiy >= (in.H + 3) / 4) return;
+    raycast_warp_tile<MODE, false, 2>(s, in, T, vtx, nrm, max_iter, tB_m, inv_sv, nullptr, nullptr, 0, tix, tiy);
 }
 
 template <int MODE, bool RANGE>
@@ -209,6 +226,11 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
             e = launch_pdl(raycast_dynamic_kernel<1>, dim3(g), dim3(256), 0, st, s, in, T_wc, vtx, nrm, max_iter, tBm,
                            inv_sv, (const uint32_t *)s.range_min, (const uint32_t *)s.range_max, tx, n_tiles, hdr_w,
                            list_w, hdr_r, list_r, use_order, write_order);
+        if (e != cudaSuccess) return e;
+        if (mode == 0)
+            e = launch_pdl(raycast_finish_kernel<0>, grid, dim3(256), 0, st, s, in, T_wc, vtx, nrm, max_iter, tBm, inv_sv);
+        else
+            e = launch_pdl(raycast_finish_kernel<1>, grid, dim3(256), 0, st, s, in, T_wc, vtx, nrm, max_iter, tBm, inv_sv);
         if (e != cudaSuccess) return e;
         if (write_order) {
             order_dims[0] = tx;
