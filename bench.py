@@ -930,6 +930,50 @@ def run_learned_section(itm, torch, dev, conf_frames):
     ms_over = float(np.mean([a.elapsed_time(b) for a, b in over]))
     same = bool(torch.equal(wpx_o, wpx))
     sc_o.close()
+    # back to back (no L2 flush between frames), through the public calls:
+    # the weights of frame k+1 on a second stream while frame k is allocated,
+    # fused and raycast; beside it the constant weight, itm_process_frame back
+    # to back on the same frames
+    sc_p = itm.Scene(**dict(w.params, weight_mode=1))
+    sc_q = itm.Scene(**w.params)
+    aux = torch.cuda.Stream(device=dev)
+    wbuf = [torch.empty_like(wpx), torch.empty_like(wpx)]
+    done_w = [torch.cuda.Event(), torch.cuda.Event()]
+    free_w = [torch.cuda.Event(), torch.cuda.Event()]
+    for j in range(2):
+        free_w[j].record(stream)
+
+    def conf_into(j):
+        aux.wait_event(free_w[j % 2])
+        itm.itm_conf_weights(dd[keys[j]], ci, mu, model.packed, wbuf[j % 2], aux)
+        done_w[j % 2].record(aux)
+
+    torch.cuda.synchronize()
+    e_pipe = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e_pipe[0].record(stream)
+    aux.wait_event(e_pipe[0])
+    conf_into(0)
+    for j, k in enumerate(keys):
+        T = ev[k][1]
+        itm.itm_allocate(sc_p.handle, dd[k], ci, T, stream)
+        stream.wait_event(done_w[j % 2])
+        itm.itm_integrate_weighted(sc_p.handle, dd[k], wbuf[j % 2], ci, T, stream)
+        free_w[j % 2].record(stream)
+        if j + 1 < len(keys):
+            conf_into(j + 1)
+        itm.itm_raycast(sc_p.handle, ci, T, vtx, nrm, stream)
+    e_pipe[1].record(stream)
+    e_plain = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e_plain[0].record(stream)
+    for k in keys:
+        itm.itm_process_frame(sc_q.handle, dd[k], ci, ev[k][1], vtx, nrm, stream)
+    e_plain[1].record(stream)
+    torch.cuda.synchronize()
+    ms_pipe = e_pipe[0].elapsed_time(e_pipe[1]) / len(keys)
+    ms_plain_b2b = e_plain[0].elapsed_time(e_plain[1]) / len(keys)
+    same_pipe = _same_volume(sc_p.export(), sc_l.export())
+    sc_p.close()
+    sc_q.close()
     rms = _rms_pair(w, sc_c.export(), sc_l.export())
     return {
         "workload": "room seed 7, 640x480 @ 5 mm, 30 frames (0, 2, ..., 58) with noise and flying pixels",
@@ -937,6 +981,15 @@ def run_learned_section(itm, torch, dev, conf_frames):
         "frames_per_s_calls_in_sequence": 1000.0 / ms,
         "plain_frames_per_s_same_frames": 1000.0 / ms_plain,
         "learned_time_over_plain": ms_over / ms_plain,
+        "back_to_back": {
+            "learned_frames_per_s": 1000.0 / ms_pipe,
+            "plain_frames_per_s": 1000.0 / ms_plain_b2b,
+            "learned_time_over_plain": ms_pipe / ms_plain_b2b,
+            "note": "the 30 frames back to back without L2 flushes; learned: itm_conf_weights of frame k+1 "
+                    "on a second stream while frame k runs itm_allocate, itm_integrate_weighted and "
+                    "itm_raycast (double-buffered weight maps); plain: itm_process_frame; the learned "
+                    "volume equals the flushed sequential run's: %s" % same_pipe,
+        },
         "overlap": "itm_process_frame_weighted: the per-pixel weights on the scene's second stream beside the "
                    "allocation, joined before the weighted integration (last frame's weight map equal to the "
                    "sequential run's: %s)" % same,
@@ -949,6 +1002,17 @@ def run_learned_section(itm, torch, dev, conf_frames):
                      "seconds": train_s},
         "rms_tsdf_error_m": rms,
     }
+
+
+def _same_volume(a, b):
+    """Two exports (coords, sdf, w) hold the same blocks and voxels (in any
+    allocation order)."""
+    ca, Fa, Wa = (np.asarray(x) for x in a)
+    cb, Fb, Wb = (np.asarray(x) for x in b)
+    if ca.shape != cb.shape:
+        return False
+    oa, ob = np.lexsort(ca.T[::-1]), np.lexsort(cb.T[::-1])
+    return bool(np.array_equal(ca[oa], cb[ob]) and np.array_equal(Fa[oa], Fb[ob]) and np.array_equal(Wa[oa], Wb[ob]))
 
 
 def _rms_pair(w, const, learned_):
