@@ -393,23 +393,46 @@ def _rot_y(deg):
     return R
 
 
+@pytest.mark.parametrize("weighted", [False, True])
 @pytest.mark.parametrize("change", ["pose", "intrinsics"])
-def test_integration_at_another_pose_than_the_allocation(itm, change):
+def test_integration_at_another_pose_than_the_allocation(itm, change, weighted):
     """The visible list marks blocks whose voxels all project inside the image
     for the allocation's pose and intrinsics, and the integration then skips
     their bounds tests.  Integrating at another pose (10 degrees of yaw) or
     with other intrinsics (cx shifted by 40 px) must not use those marks:
     every block the GPU changes equals the oracle's integration of it at the
     new pose (the oracle integrates every allocated block, the GPU the
-    allocation's visible list, so only the blocks the GPU changed compare)."""
+    allocation's visible list, so only the blocks the GPU changed compare).
+    weighted: float weights, with a seeded per-pixel weight map in (0, 1]
+    (zeros on a tenth of the pixels) on both sides."""
     w = kinect_workload(seed=3)
-    g, o, _ = run_pair(itm, w, range(3))
     ci = intr_of(itm, w.intr)
     ia = w.intr.as_array()
+    rng = np.random.default_rng(11)
+
+    def weight_map(shape):
+        m = rng.uniform(0.05, 1.0, size=shape).astype(np.float32)
+        m[rng.random(shape) < 0.1] = 0.0
+        return m
+
+    if weighted:
+        p = dict(w.params, weight_mode=1)
+        g, o = itm.Scene(**p), oracle.Scene(**p)
+        for k in range(3):
+            fk = w.frame(k)
+            m = weight_map(fk.depth.shape)
+            dk = dev(fk.depth)
+            g.allocate(dk, ci, fk.T_wc)
+            g.integrate(dk, ci, fk.T_wc, wpx=dev(m))
+            o.allocate(fk.depth, ia, fk.T_wc)
+            o.integrate(fk.depth, ia, fk.T_wc, m)
+    else:
+        g, o, _ = run_pair(itm, w, range(3))
     f = w.frame(3)
     d = dev(f.depth)
     g.allocate(d, ci, f.T_wc)
     o.allocate(f.depth, ia, f.T_wc)
+    wpx = weight_map(f.depth.shape) if weighted else None
     T2, ci2, ia2 = f.T_wc, ci, ia
     if change == "pose":
         T2 = (np.asarray(f.T_wc, np.float64) @ _rot_y(10.0)).astype(np.float32)
@@ -418,8 +441,8 @@ def test_integration_at_another_pose_than_the_allocation(itm, change):
         ci2 = itm.make_intrinsics(i2.width, i2.height, i2.fx, i2.fy, i2.cx + 40.0, i2.cy)
         ia2 = np.array([i2.fx, i2.fy, i2.cx + 40.0, i2.cy], dtype=np.float32)
     before = g.export()
-    g.integrate(d, ci2, T2)
-    o.integrate(f.depth, ia2, T2)
+    g.integrate(d, ci2, T2, wpx=None if wpx is None else dev(wpx))
+    o.integrate(f.depth, ia2, T2, wpx)
     after = g.export()
     cg, Fg, Wg = after
     assert np.array_equal(before[0], cg)
