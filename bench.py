@@ -493,7 +493,7 @@ def run_batched_section(itm, torch, dev, frames_main, small_frames, n_steps, war
         "ms_per_step": ms / n_steps,
         "items_per_step_mean": n_items / n_steps,
         "steps": n_steps,
-        "launches_per_step": 8,
+        "launches_per_step": 9,
         "cuda_graph": True,
         "l2": "flushed between steps",
         "autotune": {

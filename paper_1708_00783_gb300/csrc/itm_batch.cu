@@ -231,9 +231,29 @@ __global__ void __launch_bounds__(256, 4) batch_raycast_kernel(const ItemDev *__
         const ItemDev &it = items[k];
         if (!it.raycast) continue;
         const int local = vt - begin[k];
-        raycast_tile<0, true>(it.s, it.in, it.T, it.vtx, it.nrm, it.max_iter, it.tB_m, it.inv_sv, it.s.range_min,
-                              it.s.range_max, it.rtiles_x, it.rtiles_y, local % it.cta_tiles_x,
-                              local / it.cta_tiles_x);
+        raycast_tile<0, true, 1>(it.s, it.in, it.T, it.vtx, it.nrm, it.max_iter, it.tB_m, it.inv_sv,
+                                 it.s.range_min, it.s.range_max, it.rtiles_x, it.rtiles_y, local % it.cta_tiles_x,
+                                 local / it.cta_tiles_x);
+    }
+}
+
+// The raycast's second phase over the same tiles: refinement, hit point and
+// normal of the rays the march (batch_raycast_kernel) left behind the surface.
+__global__ void __launch_bounds__(256, 4) batch_finish_kernel(const ItemDev *__restrict__ items, const BatchHead *head,
+                                                                  bool scatter)
+{
+    __shared__ int begin[kMaxItems + 1];
+    const int n = head->n, total = head->cta_total, p = head->scatter_p;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) begin[i] = items[i].cta_begin;
+    __syncthreads();
+    for (int v = blockIdx.x; v < total; v += gridDim.x) {
+        const int vt = walk_tile(v, total, p, scatter);
+        const int k = find_item(begin, n, vt);
+        const ItemDev &it = items[k];
+        if (!it.raycast) continue;
+        const int local = vt - begin[k];
+        raycast_tile<0, false, 2>(it.s, it.in, it.T, it.vtx, it.nrm, it.max_iter, it.tB_m, it.inv_sv, nullptr,
+                                  nullptr, it.rtiles_x, it.rtiles_y, local % it.cta_tiles_x, local / it.cta_tiles_x);
     }
 }
 
@@ -332,6 +352,7 @@ static cudaError_t launch_stages(itm_batch *b, cudaStream_t st)
                                                                                         make_float2(-0.0f, -0.0f));
     batch_range_kernel<<<b->grid[ST_RANGE], 256, 0, st>>>(it, h);
     batch_raycast_kernel<<<b->grid[ST_RAYCAST], 256, 0, st>>>(it, h, b->knob[K_RAY_SCATTER] != 0);
+    batch_finish_kernel<<<b->grid[ST_RAYCAST], 256, 0, st>>>(it, h, b->knob[K_RAY_SCATTER] != 0);
     return cudaGetLastError();
 }
 
