@@ -94,21 +94,46 @@ __global__ void __launch_bounds__(kThreads) colour_kernel(SceneDev s, const floa
         const float yy = fmul(M.m[5], py), yz = fmul(M.m[6], pz);
         const float zy = fmul(M.m[9], py), zz = fmul(M.m[10], pz);
         const float gx0 = (float)(b.x * 8);
+        // the eight voxels' pixels first, then their depth reads together, then
+        // the decisions and the colour updates (as the integration orders them)
+        int pix[8];
+        float Zk[8];
+        unsigned valid = 0;
+#pragma unroll
         for (int k = 0; k < 8; ++k) {
             const float px = fmul(fadd(gx0, (float)k), vs);
             const float Z = fadd(fadd(fadd(fmul(M.m[8], px), zy), zz), M.m[11]);
+            Zk[k] = Z;
+            pix[k] = 0;
             if (Z <= 0.0f) continue;
             const float X = fadd(fadd(fadd(fmul(M.m[0], px), xy), xz), M.m[3]);
             const float Y = fadd(fadd(fadd(fmul(M.m[4], px), yy), yz), M.m[7]);
             const float u = fadd(fdiv(fmul(in.fx, X), Z), in.cx);
             const float v = fadd(fdiv(fmul(in.fy, Y), Z), in.cy);
             if (u < 1.0f || u > umax || v < 1.0f || v > vmax) continue;
-            const int pix = (int)fadd(u, 0.5f) + (int)fadd(v, 0.5f) * in.W;
-            if (pix < 0 || pix >= in.W * in.H) continue;
-            const float d = __ldg(&depth[pix]);
-            if (!(d > 0.0f)) continue;
-            const float eta = fsub(d, Z);
-            if (eta < neg_mu || eta > mu) continue;
+            const int p = (int)fadd(u, 0.5f) + (int)fadd(v, 0.5f) * in.W;
+            if (p < 0 || p >= in.W * in.H) continue;
+            pix[k] = p;
+            valid |= 1u << k;
+        }
+        float dk[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) dk[k] = (valid & (1u << k)) ? __ldg(&depth[pix[k]]) : 0.0f;
+        unsigned band = 0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            if (!(valid & (1u << k)) || !(dk[k] > 0.0f)) continue;
+            const float eta = fsub(dk[k], Zk[k]);
+            if (!(eta < neg_mu || eta > mu)) band |= 1u << k;
+        }
+        while (band) {
+            const int k = __ffs(band) - 1;
+            band &= band - 1;
+            // the voxel's camera coordinates again, with the same operations
+            const float px = fmul(fadd(gx0, (float)k), vs);
+            const float X = fadd(fadd(fadd(fmul(M.m[0], px), xy), xz), M.m[3]);
+            const float Y = fadd(fadd(fadd(fmul(M.m[4], px), yy), yz), M.m[7]);
+            const float Z = fadd(fadd(fadd(fmul(M.m[8], px), zy), zz), M.m[11]);
             colour_update(&rgbw[(size_t)ptr * kBlockVoxels + 8 * t + k], X, Y, Z, cf, max_w);
         }
     }
