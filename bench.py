@@ -1355,9 +1355,9 @@ def run_ours(args, world, rank, local):
         "cpu_baseline_threaded": cpu_mt,
         "clocks": clocks,
         "e2e": e2e,
-        # per frame: counter reset, enumerate (+ u16), commit (+ overflow), visible + range, integrate, tile
-        # queue reset, raycast march, raycast finish
-        "gpu_launches": 8 * args.steps,
+        # per frame: counter reset, enumerate (+ u16), commit (+ overflow), visible + range, integrate, raycast
+        # march, raycast finish (which clears the next raycast's tile-queue header)
+        "gpu_launches": 7 * args.steps,
         "batched": batched_rep,
         "learned": learned_rep,
         "tracking": tracking_rep,

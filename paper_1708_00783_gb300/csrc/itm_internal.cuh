@@ -310,8 +310,9 @@ struct itm_scene {
     long long range_epoch;
     float range_pose[16];
     itm_intrinsics range_intr;
-    // the tile queues of side 1 - order_side hold every tile of a tiles_x x
-    // tiles_y image ({0, 0}: none yet); the next raycast writes side order_side
+    // the tile queues of side 1 - (order_side & 1) hold every tile of a
+    // tiles_x x tiles_y image ({0, 0}: none yet); the next raycast writes side
+    // order_side & 1, whose header is already clear when bit 1 is set
     int order_dims[2];
     int order_side;
     // the visible list's interior flags were computed for vis_pose /

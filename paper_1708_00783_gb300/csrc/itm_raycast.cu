@@ -131,13 +131,16 @@ __global__ void __launch_bounds__(256, 4) raycast_dynamic_kernel(SceneDev s, Int
 }
 
 // second phase of the split raycast: refinement, hit point and normal of the
-// pixels whose march (raycast_dynamic_kernel) ended behind the surface
+// pixels whose march (raycast_dynamic_kernel) ended behind the surface.
+// hdr_clear (or null): the tile-queue header the march read, cleared for the
+// next raycast, which writes that side (so it needs no clearing launch).
 template <int MODE>
 __global__ void __launch_bounds__(256, 4) raycast_finish_kernel(SceneDev s, Intr in, Mat34 T, float4 *__restrict__ vtx,
                                                              float4 *__restrict__ nrm, int max_iter, float tB_m,
-                                                             float inv_sv)
+                                                             float inv_sv, int32_t *__restrict__ hdr_clear)
 {
     grid_dep_wait();
+    if (hdr_clear && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x < kTileHdrInts) hdr_clear[threadIdx.x] = 0;
     const int warp = threadIdx.x >> 5;
     const int tix = blockIdx.x * 4 + (warp & 3), tiy = blockIdx.y * 2 + (warp >> 2);
     if (tix >= (in.W + 7) / 8 || tiy >= (in.H + 3) / 4) return;
@@ -197,11 +200,16 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
     if (range_fits(in)) {
         // the allocation of this frame may have filled the range already
         cudaError_t e = range_ready ? cudaSuccess : launch_raycast_range(s, in, M_d, s.range_min, s.range_max, st);
+        // bit 1 of order_side: the header of side order_side & 1 is already
+        // clear (the previous raycast's finish kernel cleared it); it is
+        // dropped first, so that a launch error below leaves it unset
         const int w = order_side & 1;
+        const bool pre_cleared = (order_side & 2) != 0;
+        order_side = w;
         int32_t *hdr_w = s.tile_q_hdr + w * kTileHdrInts, *list_w = s.tile_q_list + (size_t)w * kTileClasses * kOrderMaxTiles;
         const int32_t *hdr_r = s.tile_q_hdr + (1 - w) * kTileHdrInts;
         const int32_t *list_r = s.tile_q_list + (size_t)(1 - w) * kTileClasses * kOrderMaxTiles;
-        if (e == cudaSuccess) e = launch_pdl(zero_words_kernel, dim3(1), dim3(32), 0, st, hdr_w, kTileHdrInts);
+        if (e == cudaSuccess && !pre_cleared) e = launch_pdl(zero_words_kernel, dim3(1), dim3(32), 0, st, hdr_w, kTileHdrInts);
         if (e != cudaSuccess) return e;
         static int g_dyn[2] = {0, 0};
         const int mode = s.weight_mode ? 1 : 0;
@@ -227,15 +235,20 @@ cudaError_t launch_raycast(const SceneDev &s, const Intr &in, const Mat34 &T_wc,
                            inv_sv, (const uint32_t *)s.range_min, (const uint32_t *)s.range_max, tx, n_tiles, hdr_w,
                            list_w, hdr_r, list_r, use_order, write_order);
         if (e != cudaSuccess) return e;
+        // with write_order the next raycast writes side 1 - w, which this
+        // one only read: the finish kernel clears its header
+        int32_t *hdr_clear = write_order ? s.tile_q_hdr + (1 - w) * kTileHdrInts : nullptr;
         if (mode == 0)
-            e = launch_pdl(raycast_finish_kernel<0>, grid, dim3(256), 0, st, s, in, T_wc, vtx, nrm, max_iter, tBm, inv_sv);
+            e = launch_pdl(raycast_finish_kernel<0>, grid, dim3(256), 0, st, s, in, T_wc, vtx, nrm, max_iter, tBm, inv_sv,
+                           hdr_clear);
         else
-            e = launch_pdl(raycast_finish_kernel<1>, grid, dim3(256), 0, st, s, in, T_wc, vtx, nrm, max_iter, tBm, inv_sv);
+            e = launch_pdl(raycast_finish_kernel<1>, grid, dim3(256), 0, st, s, in, T_wc, vtx, nrm, max_iter, tBm, inv_sv,
+                           hdr_clear);
         if (e != cudaSuccess) return e;
         if (write_order) {
             order_dims[0] = tx;
             order_dims[1] = ty;
-            order_side = 1 - w;
+            order_side = (1 - w) | 2;
         }
         return cudaSuccess;
     } else {
