@@ -453,3 +453,29 @@ def test_integration_at_another_pose_than_the_allocation(itm, change, weighted):
     io = np.array([pos[k] for k in key_of(cg[changed]).tolist()])
     assert np.array_equal(Wg[changed], Wo[io])
     assert np.abs(Fg[changed] - Fo[io]).max() <= 1e-4
+
+
+def test_raycast_wider_than_the_search_range_images(itm):
+    """An image wider than the search-range tiles cover (4096 pixels) takes
+    the raycast without a search range (one kernel, raster tiles): a
+    4104 x 24 strip through the tiny scene's centre, a few pixels of it
+    ragged against the warp tiles, equals the oracle's raycast within the
+    raycast tolerance, twice in a row (the tile queues are not involved)."""
+    import torch
+    w = tiny_workload()
+    g, o, _ = run_pair(itm, w, range(w.n_frames))
+    T = w.frame(5).T_wc
+    Wd, Hd = 4104, 24
+    strip = Intrinsics(Wd, Hd, w.intr.fx, w.intr.fy, (Wd - 1) / 2.0, (Hd - 1) / 2.0)
+    cs = intr_of(itm, strip)
+    outs = []
+    for _ in range(2):
+        v = torch.zeros((Hd, Wd, 4), dtype=torch.float32, device="cuda")
+        n = torch.zeros_like(v)
+        g.raycast(cs, T, v, n)
+        torch.cuda.synchronize()
+        outs.append((v.cpu().numpy(), n.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    vo, no = o.raycast(Wd, Hd, strip.as_array(), T)
+    rep = compare_raycast(outs[0][0], outs[0][1], vo, no, T)
+    assert rep["hits"] > 1000
