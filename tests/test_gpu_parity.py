@@ -479,3 +479,27 @@ def test_raycast_wider_than_the_search_range_images(itm):
     vo, no = o.raycast(Wd, Hd, strip.as_array(), T)
     rep = compare_raycast(outs[0][0], outs[0][1], vo, no, T)
     assert rep["hits"] > 1000
+
+
+def test_fusion_of_an_image_wider_than_the_search_range_images(itm):
+    """Allocation and integration of a frame wider than the search-range
+    tiles cover (4104 x 24, rendered from the tiny scene without noise):
+    the allocation then builds the visible list without a search range, and
+    the volume after it equals the oracle's (block set and weights exact,
+    sdf within 1e-4)."""
+    w = tiny_workload()
+    g, o, _ = run_pair(itm, w, range(3))
+    T = w.frame(4).T_wc
+    Wd, Hd = 4104, 24
+    strip = Intrinsics(Wd, Hd, w.intr.fx, w.intr.fy, (Wd - 1) / 2.0, (Hd - 1) / 2.0)
+    z = w.scene.render(strip, T)[0].astype(np.float32)
+    z[(z < w.params["z_min"]) | (z > w.params["z_max"])] = 0.0
+    assert np.count_nonzero(z) > 2000
+    cs = intr_of(itm, strip)
+    d = dev(z)
+    g.allocate(d, cs, T)
+    g.integrate(d, cs, T)
+    o.allocate(z, strip.as_array(), T)
+    o.integrate(z, strip.as_array(), T)
+    assert g.status() == 0
+    compare_volumes(g.export(), o.export())
